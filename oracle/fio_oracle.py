@@ -1,0 +1,258 @@
+"""Oracle for the discrete FIO u = K f-hat: the plain definition, in FP64 on the CPU.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): nothing in the product imports this module.
+
+What it follows (paper section and equation; the paper numbers equations per section):
+  * Grids X and Omega: section 1, the definitions of X and Omega (x = n_k/n in [0,1)^d,
+    xi integer in [-n/2, n/2)^d, n even).
+  * The matrix K_ij = a(x_i, xi_j) exp(2 pi i Phi(x_i, xi_j)): section 1, eq. (1.3) and the
+    sentence after eq. (1.6).  No normalisation: the 1/n^d belongs to the DFT F only.
+  * Example 1 (section 6): a = 1, Phi = x xi + c(x)|xi|, c(x) = (2 + sin 2 pi x)/8,
+    x_i = i/N, xi_j = j - N/2 (the paper writes the same grid 1-based).
+  * Example 3 (section 6): a = 1, Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2),
+    c1 = (2 + sin 2pi x1 sin 2pi x2)/16, c2 = (2 + cos 2pi x1 cos 2pi x2)/16.
+  * "linear": Phi = x.xi, a = 1 (Example 1 with c = 0).  Then K is diag((-1)^i) times the
+    unnormalised inverse DFT (closed form used as a pin).
+
+Readings where the paper is silent:
+  * 2D linear index: point (i1, i2) has index i1 + n*i2, for X and for Omega alike.
+  * |xi| and the square root are 0 at xi = 0, so that column of K is exp(2 pi i x.xi) = 1.
+  * Argument reduction: x.xi = (sum_d i_d xi_d)/n is reduced exactly in integers modulo n;
+    the smooth part is reduced by theta - round(theta) before exp(2 pi i theta).
+
+Functions and their pins (tests/test_oracle.py):
+  grid, phase_frac, K_block, dense_K      pinned: DFT closed form (numpy.fft), hand-computed
+                                          golden rows (tests/golden/), |K_ij| = 1
+  apply_K, apply_Kadj, K_rows             pinned: dense product, DFT closed form, <Kf,u> = <f,K*u>
+  solve_lu                                pinned: Gauss-Jordan brute force, K^{-1} = K*/N (linear)
+  gauss_jordan_solve                      pinned: identity / permutation / closed-form 2x2 cases
+  normal_matrix                           pinned: diag = N exactly, Hermitian positive definite,
+                                          = N I for the linear phase
+  cgne                                    pinned: agrees with solve_lu; true residual
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg
+
+KINDS = ("ex1", "ex3", "linear1d", "linear2d")
+
+
+@dataclass(frozen=True)
+class FIO:
+    """A discrete FIO on an n^d grid (section 1).  kind selects the phase of section 6."""
+
+    kind: str
+    n: int
+
+    @property
+    def d(self) -> int:
+        return 1 if self.kind in ("ex1", "linear1d") else 2
+
+    @property
+    def N(self) -> int:
+        return self.n ** self.d
+
+
+def grid(op: FIO, idx: np.ndarray):
+    """Integer grid coordinates of linear indices idx (same map for X and Omega).
+
+    Returns (k, xi): k[:, t] in [0, n) gives x_t = k_t / n; xi[:, t] = k_t - n/2 in [-n/2, n/2).
+    """
+    idx = np.asarray(idx, dtype=np.int64)
+    n = op.n
+    if op.d == 1:
+        k = idx[:, None]
+    else:
+        k = np.stack([idx % n, idx // n], axis=1)
+    return k, k - n // 2
+
+
+def phase_frac(op: FIO, rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
+    """Phase Phi(x_rows, xi_cols) reduced to [-1/2, 1/2] (only exp(2 pi i Phi) is needed).
+
+    Returns an array of shape (len(rows), len(cols)).
+    """
+    n = op.n
+    kx, _ = grid(op, rows)
+    _, xi = grid(op, cols)
+    # exact part x.xi = (sum_t k_t * xi_t) / n, reduced modulo n in integers
+    num = np.zeros((len(kx), len(xi)), dtype=np.int64)
+    for t in range(op.d):
+        num += np.outer(kx[:, t], xi[:, t])
+    lin = np.mod(num, n).astype(np.float64) / n
+    x = kx.astype(np.float64) / n
+    if op.kind == "ex1":
+        c = (2.0 + np.sin(2.0 * np.pi * x[:, 0])) / 8.0
+        smooth = np.outer(c, np.abs(xi[:, 0]).astype(np.float64))
+    elif op.kind == "ex3":
+        s = np.sin(2.0 * np.pi * x)
+        co = np.cos(2.0 * np.pi * x)
+        c1 = (2.0 + s[:, 0] * s[:, 1]) / 16.0
+        c2 = (2.0 + co[:, 0] * co[:, 1]) / 16.0
+        xi1 = xi[:, 0].astype(np.float64)
+        xi2 = xi[:, 1].astype(np.float64)
+        smooth = np.sqrt(np.outer(c1 * c1, xi1 * xi1) + np.outer(c2 * c2, xi2 * xi2))
+    elif op.kind in ("linear1d", "linear2d"):
+        smooth = np.zeros_like(lin)
+    else:
+        raise ValueError(f"unknown kind {op.kind!r}")
+    smooth = smooth - np.round(smooth)
+    theta = lin + smooth
+    return theta - np.round(theta)
+
+
+def K_block(op: FIO, rows, cols) -> np.ndarray:
+    """Entries K[rows, cols] = a exp(2 pi i Phi) with a = 1 (eq. 1.3)."""
+    theta = phase_frac(op, np.asarray(rows), np.asarray(cols))
+    return np.exp(2j * np.pi * theta)
+
+
+def dense_K(op: FIO) -> np.ndarray:
+    """The dense N x N matrix K (eq. 1.6)."""
+    idx = np.arange(op.N)
+    return K_block(op, idx, idx)
+
+
+def K_rows(op: FIO, rows, f: np.ndarray, chunk: int = 64) -> np.ndarray:
+    """(K f)[rows, :] computed one row chunk at a time, O(N) memory per row (matrix-free)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    f = np.asarray(f, dtype=np.complex128)
+    squeeze = f.ndim == 1
+    if squeeze:
+        f = f[:, None]
+    cols = np.arange(op.N)
+    out = np.empty((len(rows), f.shape[1]), dtype=np.complex128)
+    for s in range(0, len(rows), chunk):
+        blk = K_block(op, rows[s:s + chunk], cols)
+        out[s:s + chunk] = blk @ f
+    return out[:, 0] if squeeze else out
+
+
+def apply_K(op: FIO, f: np.ndarray, chunk: int = 64) -> np.ndarray:
+    """u = K f (eq. 1.6), matrix-free by row chunks."""
+    return K_rows(op, np.arange(op.N), f, chunk)
+
+
+def apply_Kadj(op: FIO, u: np.ndarray, chunk: int = 64) -> np.ndarray:
+    """K* u, K* the conjugate transpose of K (adjoint of eq. 1.6)."""
+    u = np.asarray(u, dtype=np.complex128)
+    squeeze = u.ndim == 1
+    if squeeze:
+        u = u[:, None]
+    cols = np.arange(op.N)
+    out = np.zeros((op.N, u.shape[1]), dtype=np.complex128)
+    for s in range(0, op.N, chunk):
+        rows = np.arange(s, min(op.N, s + chunk))
+        blk = K_block(op, rows, cols)
+        out += blk.conj().T @ u[rows]
+    return out[:, 0] if squeeze else out
+
+
+def solve_lu(op: FIO, u: np.ndarray, K: np.ndarray | None = None) -> np.ndarray:
+    """f-hat = K^{-1} u by dense LU with partial pivoting (LAPACK getrf/getrs as one step)."""
+    if K is None:
+        K = dense_K(op)
+    lu, piv = scipy.linalg.lu_factor(K)
+    return scipy.linalg.lu_solve((lu, piv), np.asarray(u, dtype=np.complex128))
+
+
+def gauss_jordan_solve(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Brute-force Gauss-Jordan elimination with partial pivoting, row by row in Python.
+
+    For tiny systems only (N <= 64); an independent check of solve_lu.
+    """
+    A = np.array(A, dtype=np.complex128)
+    B = np.array(B, dtype=np.complex128)
+    squeeze = B.ndim == 1
+    if squeeze:
+        B = B[:, None]
+    n = A.shape[0]
+    aug = [list(A[i]) + list(B[i]) for i in range(n)]
+    for col in range(n):
+        piv = max(range(col, n), key=lambda r: abs(aug[r][col]))
+        if abs(aug[piv][col]) == 0.0:
+            raise np.linalg.LinAlgError("singular matrix")
+        aug[col], aug[piv] = aug[piv], aug[col]
+        p = aug[col][col]
+        aug[col] = [v / p for v in aug[col]]
+        for r in range(n):
+            if r != col and aug[r][col] != 0:
+                fac = aug[r][col]
+                aug[r] = [a - fac * b for a, b in zip(aug[r], aug[col])]
+    X = np.array([row[n:] for row in aug], dtype=np.complex128)
+    return X[:, 0] if squeeze else X
+
+
+def normal_matrix(op: FIO, K: np.ndarray | None = None) -> np.ndarray:
+    """S = K* K (section 3.1, the discrete normal matrix)."""
+    if K is None:
+        K = dense_K(op)
+    return K.conj().T @ K
+
+
+def cgne(op: FIO, u: np.ndarray, tol: float = 1e-13, maxit: int = 500, K: np.ndarray | None = None):
+    """Conjugate gradients on K* K f = K* u (the normal equations, section 5), FP64.
+
+    Matrix-free unless a dense K is passed.  Returns (f, iterations, true relative residual
+    ||u - K f|| / ||u||) per column.
+    """
+    u = np.asarray(u, dtype=np.complex128)
+    squeeze = u.ndim == 1
+    if squeeze:
+        u = u[:, None]
+    if K is not None:
+        mv = lambda v: K @ v  # noqa: E731
+        mva = lambda v: K.conj().T @ v  # noqa: E731
+    else:
+        mv = lambda v: apply_K(op, v)  # noqa: E731
+        mva = lambda v: apply_Kadj(op, v)  # noqa: E731
+    b = mva(u)
+    f = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = np.sum(np.abs(r) ** 2, axis=0)
+    bnorm = np.sqrt(np.sum(np.abs(b) ** 2, axis=0))
+    it = 0
+    for it in range(1, maxit + 1):
+        q = mva(mv(p))
+        alpha = rr / np.real(np.sum(p.conj() * q, axis=0))
+        f += alpha * p
+        r -= alpha * q
+        rr_new = np.sum(np.abs(r) ** 2, axis=0)
+        if np.all(np.sqrt(rr_new) <= tol * bnorm):
+            rr = rr_new
+            break
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    res = mv(f) - u
+    relres = np.sqrt(np.sum(np.abs(res) ** 2, axis=0)) / np.sqrt(np.sum(np.abs(u) ** 2, axis=0))
+    if squeeze:
+        return f[:, 0], it, float(relres[0])
+    return f, it, relres
+
+
+def rel_err(a: np.ndarray, b: np.ndarray) -> float:
+    """||a - b||_F / ||b||_F."""
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def spectral_norm_est(apply, n: int, iters: int = 30, seed: int = 7) -> float:
+    """||A||_2 by power iteration on A* A given apply(x, adjoint) -> A x or A* x.
+
+    The paper estimates e_a and e_s by randomized power iteration (section 6)."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x /= np.linalg.norm(x)
+    lam = 0.0
+    for _ in range(iters):
+        y = apply(apply(x, False), True)
+        lam = np.linalg.norm(y)
+        if lam == 0:
+            return 0.0
+        x = y / lam
+    return math.sqrt(lam)

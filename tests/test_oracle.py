@@ -1,0 +1,165 @@
+"""Pins of the oracle (oracle/fio_oracle.py) against what the paper and the mathematics fix.
+
+Each test names the fact it checks.  None of them compares the oracle with itself: the expected
+values come from hand-worked phases (tests/golden/phase_values.txt), numpy.fft (a library DFT),
+closed forms, or an independent elimination.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fio_oracle as fo
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "phase_values.txt")
+
+
+def _golden_rows():
+    out = []
+    with open(GOLDEN) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            kind, n, row, col, num, den = line.split()
+            out.append((kind, int(n), int(row), int(col), int(num), int(den)))
+    return out
+
+
+def test_golden_phases():
+    """Hand-worked entries of K for Examples 1 and 3 (section 6): sign, grids, c(x), ordering."""
+    rows = _golden_rows()
+    assert len(rows) > 40
+    for kind, n, r, c, num, den in rows:
+        op = fo.FIO(kind, n)
+        got = fo.K_block(op, [r], [c])[0, 0]
+        want = np.exp(2j * np.pi * num / den)
+        assert abs(got - want) < 1e-14, (kind, n, r, c, got, want)
+
+
+@pytest.mark.parametrize("kind", ["ex1", "ex3"])
+def test_unit_modulus(kind):
+    """a = 1 in both examples, so |K_ij| = 1 (eq. 1.6)."""
+    op = fo.FIO(kind, 16)
+    K = fo.dense_K(op)
+    assert np.max(np.abs(np.abs(K) - 1.0)) < 1e-14
+
+
+@pytest.mark.parametrize("N", [8, 64, 256])
+def test_linear_phase_is_inverse_dft_1d(N):
+    """Phi = x xi (Example 1 with c = 0): K f = (-1)^i N ifft(f) (library DFT)."""
+    op = fo.FIO("linear1d", N)
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    want = ((-1.0) ** np.arange(N)) * N * np.fft.ifft(f)
+    assert fo.rel_err(fo.apply_K(op, f), want) < 1e-13
+    assert fo.rel_err(fo.dense_K(op) @ f, want) < 1e-13
+
+
+@pytest.mark.parametrize("n", [4, 8, 16])
+def test_linear_phase_is_inverse_dft_2d(n):
+    """2D Phi = x.xi with index i1 + n i2: K f = (-1)^(k1+k2) n^2 ifft2(f)."""
+    op = fo.FIO("linear2d", n)
+    rng = np.random.default_rng(2)
+    f = rng.standard_normal(n * n) + 1j * rng.standard_normal(n * n)
+    F = f.reshape(n, n)  # F[j2, j1]
+    k2, k1 = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    want = (((-1.0) ** (k1 + k2)) * n * n * np.fft.ifft2(F)).reshape(-1)
+    assert fo.rel_err(fo.apply_K(op, f), want) < 1e-13
+
+
+@pytest.mark.parametrize("kind,n", [("linear1d", 32), ("linear2d", 8)])
+def test_linear_phase_normal_matrix_is_NI(kind, n):
+    """K*K = N I and K^{-1} = K*/N for the linear phase (closed form)."""
+    op = fo.FIO(kind, n)
+    S = fo.normal_matrix(op)
+    assert np.max(np.abs(S - op.N * np.eye(op.N))) < 1e-10
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)
+    assert fo.rel_err(fo.solve_lu(op, u), fo.apply_Kadj(op, u) / op.N) < 1e-12
+
+
+@pytest.mark.parametrize("kind,n", [("ex1", 64), ("ex1", 256), ("ex3", 8), ("ex3", 16)])
+def test_normal_matrix_diag_and_hpd(kind, n):
+    """S = K*K: diag(S) = N exactly for a = 1, S Hermitian positive definite (section 3.1)."""
+    op = fo.FIO(kind, n)
+    S = fo.normal_matrix(op)
+    assert np.max(np.abs(np.diag(S) - op.N)) < 1e-9
+    assert np.max(np.abs(S - S.conj().T)) < 1e-9
+    np.linalg.cholesky(S)  # raises unless positive definite
+    assert np.linalg.eigvalsh(S).min() > 0
+
+
+def test_normal_matrix_decay_ex1():
+    """|S(xi, eta)| decays away from the diagonal (Proposition in section 3.1), qualitatively:
+    the mean modulus of the band |xi - eta| in [16, 32) is well below the diagonal value N."""
+    op = fo.FIO("ex1", 256)
+    S = np.abs(fo.normal_matrix(op))
+    i, j = np.indices(S.shape)
+    band = (np.abs(i - j) >= 16) & (np.abs(i - j) < 32)
+    assert S[band].mean() < 0.05 * op.N
+
+
+def test_adjoint_identity():
+    """<K f, u> = <f, K* u> for the matrix-free products (definition of the adjoint)."""
+    op = fo.FIO("ex1", 128)
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)
+    u = rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)
+    lhs = np.vdot(u, fo.apply_K(op, f))
+    rhs = np.vdot(fo.apply_Kadj(op, u), f)
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+def test_matrix_free_rows_match_dense():
+    """Row-sampled matrix-free K f equals the dense product (chunking has no effect)."""
+    op = fo.FIO("ex3", 16)
+    K = fo.dense_K(op)
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal((op.N, 3)) + 1j * rng.standard_normal((op.N, 3))
+    rows = np.array([0, 5, 77, 255])
+    assert fo.rel_err(fo.K_rows(op, rows, f, chunk=3), (K @ f)[rows]) < 1e-14
+
+
+def test_gauss_jordan_known_cases():
+    """Gauss-Jordan on closed-form systems: a permutation and a 2x2 with a known inverse."""
+    P = np.array([[0, 1, 0], [0, 0, 1], [1, 0, 0]], dtype=complex)
+    b = np.array([1.0, 2.0, 3.0 + 1j])
+    assert np.allclose(fo.gauss_jordan_solve(P, b), [3.0 + 1j, 1.0, 2.0])
+    A = np.array([[2, 1j], [-1j, 3]], dtype=complex)  # det = 5, inverse = [[3, -i], [i, 2]] / 5
+    Ainv = np.array([[3, -1j], [1j, 2]]) / 5
+    assert np.allclose(fo.gauss_jordan_solve(A, np.eye(2)), Ainv, atol=1e-15)
+
+
+@pytest.mark.parametrize("kind,n", [("ex1", 32), ("ex1", 64), ("ex3", 8)])
+def test_lu_matches_gauss_jordan(kind, n):
+    """Dense LU solve vs the brute-force elimination at N <= 64."""
+    op = fo.FIO(kind, n)
+    rng = np.random.default_rng(6)
+    u = rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)
+    f_lu = fo.solve_lu(op, u)
+    f_gj = fo.gauss_jordan_solve(fo.dense_K(op), u)
+    assert fo.rel_err(f_lu, f_gj) < 1e-11
+    assert fo.rel_err(fo.apply_K(op, f_lu), u) < 1e-11
+
+
+def test_cgne_matches_lu():
+    """CG on the normal equations (section 5) reaches the LU solution and a small true residual."""
+    op = fo.FIO("ex1", 256)
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)
+    K = fo.dense_K(op)
+    f, it, res = fo.cgne(op, u, tol=1e-13, K=K)
+    assert res < 1e-10
+    assert it < 200
+    assert fo.rel_err(f, fo.solve_lu(op, u, K=K)) < 1e-9
+
+
+def test_planted_sign_error_is_caught():
+    """A conjugated kernel (wrong sign of the phase) fails the golden and the DFT pins."""
+    op = fo.FIO("linear1d", 16)
+    K = fo.dense_K(op).conj()
+    f = np.arange(16) + 1j
+    want = ((-1.0) ** np.arange(16)) * 16 * np.fft.ifft(f)
+    assert fo.rel_err(K @ f, want) > 0.1
