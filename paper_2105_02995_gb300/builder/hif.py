@@ -1,0 +1,362 @@
+"""Inverse of the hierarchical matrix S-dot by recursive skeletonization / HIF (section 4).
+
+For l = L_H down to the stop level, on the active DOFs S_l:
+  * Cell skeletonization (section 4.1; 4.2 for 2D): for each cell with active DOFs I, build
+    U-bar = [A_BI; far-field rows] (eq. for U-bar; in 2D the near field A_BI on the neighbour list
+    and, for every level l' <= l, the rows B U* of the admissible blocks of the cell's ancestor,
+    eq. for the 2D bases), compute an interpolative decomposition U-bar_{I~} ~ U-bar_{I^} T by
+    column-pivoted QR truncated at eps (eq. 4.x, the ID), then the zeroing matrix Z_I and
+    the elimination matrix E_I (eq. for Z and eq. for E):
+        A~_rr = A_rr - T* A_sr - A_sr* T + T* A_ss T,   A~_sr = A_sr - A_ss T,
+        A~_rr = L L*,  W = A~_sr A~_rr^{-1},  A_ss <- A_ss - W A~_sr*.
+  * Edge skeletonization (2D only, section 4.2): every active DOF is assigned to the nearest edge
+    of its cell; each edge's DOFs (from its two cells) are skeletonized the same way with
+    U-bar = [A_BI1 A_BI2; far(I1) (+) far(I2)] (eq. for the edge U-bar).
+  * Merge: active DOFs of sibling cells are concatenated (the parent's near field is assembled from
+    the children's near blocks and the level-l admissible blocks between them).
+Finally A_0, the matrix on the remaining active DOFs, is formed densely and inverted.
+
+Every node contributes the dense matrix (Z_I E_I)* on its index set, ordered (I~, I^):
+        (Z E)* = [[L^{-1}, -L^{-1} T*], [-W, I + W T*]],
+one INPLACE block of the stage R_l* (or Rbar_l*); the root stage holds A_0^{-1}.  Then
+        G-dot = R_L ... R_1 A_0^{-1} R_1* ... R_L*   (1D, eq. for G-dot)
+and the 2D product with Rbar_l between the cell factors (eq. for G-dot in 2D).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from .hmatrix import HMatrix
+from .stages import KIND_INPLACE, ROLE_HIF_CELL, ROLE_HIF_EDGE, ROLE_ROOT, Stage
+
+
+def interp_decomp(Ub: np.ndarray, eps: float, ncols: int):
+    """ID by column-pivoted QR: returns (skel positions, redundant positions, T)."""
+    if Ub.shape[0] == 0 or ncols == 0:
+        return np.zeros(0, dtype=np.int64), np.arange(ncols), np.zeros((0, ncols))
+    nrm = np.linalg.norm(Ub)
+    if nrm == 0:
+        return np.zeros(0, dtype=np.int64), np.arange(ncols), np.zeros((0, ncols))
+    Q, R, P = sla.qr(Ub, mode="economic", pivoting=True)
+    diag = np.abs(np.diag(R))
+    k = int(np.count_nonzero(diag > eps * diag[0])) if diag.size else 0
+    if k == 0:
+        return np.zeros(0, dtype=np.int64), np.arange(ncols), np.zeros((0, ncols))
+    T = sla.solve_triangular(R[:k, :k], R[:k, k:], lower=False)
+    return P[:k], P[k:], T
+
+
+def eliminate(A: np.ndarray, red: np.ndarray, skel: np.ndarray, T: np.ndarray):
+    """Zeroing + Gaussian elimination of the redundant DOFs of one node (eqs. Z, E).
+
+    A: the node's dense block (Hermitian), red/skel: positions.  Returns (M, schur) with M the
+    (Z E)* matrix in (red, skel) order and schur the updated A_ss.
+    """
+    Arr = A[np.ix_(red, red)]
+    Asr = A[np.ix_(skel, red)]
+    Ass = A[np.ix_(skel, skel)]
+    TH = T.conj().T
+    Asr_t = Asr - Ass @ T
+    Arr_t = Arr - TH @ Asr - Asr.conj().T @ T + TH @ Ass @ T
+    Arr_t = 0.5 * (Arr_t + Arr_t.conj().T)
+    L = np.linalg.cholesky(Arr_t)
+    Linv = sla.solve_triangular(L, np.eye(L.shape[0], dtype=np.complex128), lower=True)
+    W = sla.cho_solve((L, True), Asr_t.conj().T).conj().T  # A~_sr A~_rr^{-1}
+    schur = Ass - W @ Asr_t.conj().T
+    schur = 0.5 * (schur + schur.conj().T)
+    nr, ns = len(red), len(skel)
+    M = np.zeros((nr + ns, nr + ns), dtype=np.complex128)
+    M[:nr, :nr] = Linv
+    M[:nr, nr:] = -Linv @ TH
+    M[nr:, :nr] = -W
+    M[nr:, nr:] = np.eye(ns) + W @ TH
+    return M, schur
+
+
+class HIF:
+    def __init__(self, H: HMatrix, eps: float, edges: bool = None, stop_level: int = None):
+        self.H = H
+        self.g = H.geom
+        self.t = self.g.tree
+        self.eps = eps
+        d = self.g.d
+        self.edges = (d == 2) if edges is None else edges
+        if stop_level is None:
+            stop_level = 1 if d == 1 else 2
+        self.stop = min(stop_level, self.g.LH)
+        self.stages = []
+        self.stats = []
+        self._far_factors()
+
+    # ---- far field -------------------------------------------------------------------------
+    def _far_factors(self):
+        """Per level l' and cell a: R factor of the stacked B U* rows of a's admissible blocks."""
+        self.far = {}
+        for lvl, lr in self.H.lowrank.items():
+            rows = {}
+            for (c, J), (U1, B, U2) in lr.blocks.items():
+                rows.setdefault(c, []).append(B @ U2.conj().T)          # A_Jc = U1 (B U2*)
+                rows.setdefault(J, []).append(B.conj().T @ U1.conj().T)  # A_cJ = U2 (B* U1*)
+            fl = {}
+            for a, lst in rows.items():
+                F = np.vstack(lst)
+                if F.shape[0] > F.shape[1]:
+                    F = sla.qr(F, mode="r")[0][: F.shape[1]]
+                fl[a] = F
+            self.far[lvl] = fl
+
+    def _far_rows(self, lvl: int, c: int, I: np.ndarray) -> list:
+        out = []
+        pos = self.t.pos[I]
+        for up in range(lvl, 0, -1):
+            a = self.g.ancestor(lvl, c, up)
+            F = self.far.get(up, {}).get(a)
+            if F is not None:
+                out.append(F[:, pos - a * self.t.size(up)])
+        return out
+
+    def _lowrank_block(self, lvl, X, Y, rows, cols):
+        """A[rows, cols] for cells X, Y admissible at `lvl` (rows/cols are global DOF ids)."""
+        size = self.t.size(lvl)
+        return self.H.lowrank[lvl].get(self.t, lvl, X, Y,
+                                       self.t.pos[rows] - X * size, self.t.pos[cols] - Y * size)
+
+    # ---- driver ----------------------------------------------------------------------------
+    def run(self):
+        g, t = self.g, self.t
+        LH = g.LH
+        self.dofs = {c: t.points(LH, c).copy() for c in range(g.beta ** LH)}
+        self.near = {k: v.copy() for k, v in self.H.near.items()}
+        for lvl in range(LH, self.stop - 1, -1):
+            self._cells(lvl)
+            if self.edges and lvl >= 2:
+                self._edges(lvl)
+            if lvl > self.stop:
+                self._merge(lvl)
+        self._root(self.stop)
+        return self.stages
+
+    def _restrict(self, c: int, keep_pos: np.ndarray, lvl: int):
+        """Drop eliminated DOFs of cell c from every near block involving c."""
+        self.dofs[c] = self.dofs[c][keep_pos]
+        for c2 in self.g.NL[lvl][c]:
+            if c2 == c:
+                self.near[(c, c)] = self.near[(c, c)][np.ix_(keep_pos, keep_pos)]
+            else:
+                self.near[(c, c2)] = self.near[(c, c2)][keep_pos]
+                self.near[(c2, c)] = self.near[(c2, c)][:, keep_pos]
+
+    def _cells(self, lvl: int):
+        g = self.g
+        st = Stage(KIND_INPLACE, self.t.N, self.t.N, ROLE_HIF_CELL, level=lvl)
+        nred = 0
+        for c in range(g.beta ** lvl):
+            I = self.dofs[c]
+            if len(I) == 0:
+                continue
+            rows = [self.near[(c2, c)] for c2 in g.NL[lvl][c] if c2 != c]
+            rows += self._far_rows(lvl, c, I)
+            Ub = np.vstack(rows) if rows else np.zeros((0, len(I)))
+            skel, red, T = interp_decomp(Ub, self.eps, len(I))
+            if len(red) == 0:
+                continue
+            M, schur = eliminate(self.near[(c, c)], red, skel, T)
+            st.add(M, np.concatenate([I[red], I[skel]]), np.concatenate([I[red], I[skel]]))
+            nred += len(red)
+            self.near[(c, c)][np.ix_(skel, skel)] = schur
+            self._restrict(c, np.sort(skel), lvl)
+        if st.blocks:
+            self.stages.append(st)
+        self.stats.append(("cell", lvl, nred, sum(len(v) for v in self.dofs.values())))
+
+    def _edge_assign(self, lvl: int):
+        """Edge of every active DOF: nearest edge of its cell, ties in the order l, r, b, t."""
+        n = self.g.n
+        m = 2 ** lvl
+        s = n // m
+        groups = {}
+        for c in range(self.g.beta ** lvl):
+            I = self.dofs[c]
+            if len(I) == 0:
+                continue
+            a1, a2 = (int(v[0]) for v in self.t.cell_coords(lvl, np.array([c])))
+            j1, j2 = I % n, I // n
+            dist = np.stack([j1 - a1 * s, (a1 + 1) * s - 1 - j1,
+                             j2 - a2 * s, (a2 + 1) * s - 1 - j2], axis=1)
+            side = np.argmin(dist, axis=1)
+            for sd in range(4):
+                sel = np.nonzero(side == sd)[0]
+                if len(sel) == 0:
+                    continue
+                if sd == 0:
+                    key = ("v", a1, a2)
+                elif sd == 1:
+                    key = ("v", (a1 + 1) % m, a2)
+                elif sd == 2:
+                    key = ("h", a1, a2)
+                else:
+                    key = ("h", a1, (a2 + 1) % m)
+                groups.setdefault(key, {})[c] = I[sel]
+        return groups
+
+    def _edges(self, lvl: int):
+        g, t = self.g, self.t
+        m = 2 ** lvl
+        st = Stage(KIND_INPLACE, t.N, t.N, ROLE_HIF_EDGE, level=lvl)
+        nred = 0
+        groups = self._edge_assign(lvl)
+        for key in sorted(groups):
+            kind, e1, e2 = key
+            if kind == "v":
+                c1 = int(t.cell_id(lvl, (e1 - 1) % m, e2))
+                c2 = int(t.cell_id(lvl, e1, e2))
+            else:
+                c1 = int(t.cell_id(lvl, e1, (e2 - 1) % m))
+                c2 = int(t.cell_id(lvl, e1, e2))
+            # current positions of the edge's DOFs (earlier edges may have shrunk the cells)
+            p1 = self._pos_of(c1, groups[key].get(c1))
+            p2 = self._pos_of(c2, groups[key].get(c2))
+            I1, I2 = self.dofs[c1][p1], self.dofs[c2][p2]
+            nI1, nI = len(I1), len(I1) + len(I2)
+            if nI == 0:
+                continue
+            # near-field rows
+            cells = np.union1d(g.NL[lvl][c1], g.NL[lvl][c2])
+            rows = []
+            for cc in cells:
+                keep = np.ones(len(self.dofs[cc]), dtype=bool)
+                if cc == c1:
+                    keep[p1] = False
+                if cc == c2:
+                    keep[p2] = False
+                if not keep.any():
+                    continue
+                blk = np.zeros((int(keep.sum()), nI), dtype=np.complex128)
+                if cc in g.NL[lvl][c1]:
+                    blk[:, :nI1] = self.near[(cc, c1)][keep][:, p1]
+                if cc in g.NL[lvl][c2]:
+                    blk[:, nI1:] = self.near[(cc, c2)][keep][:, p2]
+                rows.append(blk)
+            for part, (c, I) in enumerate(((c1, I1), (c2, I2))):
+                if len(I) == 0:
+                    continue
+                for F in self._far_rows(lvl, c, I):
+                    blk = np.zeros((F.shape[0], nI), dtype=np.complex128)
+                    if part == 0:
+                        blk[:, :nI1] = F
+                    else:
+                        blk[:, nI1:] = F
+                    rows.append(blk)
+            Ub = np.vstack(rows) if rows else np.zeros((0, nI))
+            skel, red, T = interp_decomp(Ub, self.eps, nI)
+            if len(red) == 0:
+                continue
+            A = np.empty((nI, nI), dtype=np.complex128)
+            A[:nI1, :nI1] = self.near[(c1, c1)][np.ix_(p1, p1)]
+            A[nI1:, nI1:] = self.near[(c2, c2)][np.ix_(p2, p2)]
+            A[:nI1, nI1:] = self.near[(c1, c2)][np.ix_(p1, p2)]
+            A[nI1:, :nI1] = self.near[(c2, c1)][np.ix_(p2, p1)]
+            M, schur = eliminate(A, red, skel, T)
+            I = np.concatenate([I1, I2])
+            st.add(M, np.concatenate([I[red], I[skel]]), np.concatenate([I[red], I[skel]]))
+            nred += len(red)
+            # write the Schur complement back into the near blocks
+            sk1 = skel[skel < nI1]
+            sk2 = skel[skel >= nI1] - nI1
+            o1 = skel < nI1
+            o2 = ~o1
+            S11 = schur[np.ix_(o1, o1)]
+            S22 = schur[np.ix_(o2, o2)]
+            S12 = schur[np.ix_(o1, o2)]
+            self.near[(c1, c1)][np.ix_(p1[sk1], p1[sk1])] = S11
+            self.near[(c2, c2)][np.ix_(p2[sk2], p2[sk2])] = S22
+            self.near[(c1, c2)][np.ix_(p1[sk1], p2[sk2])] = S12
+            self.near[(c2, c1)][np.ix_(p2[sk2], p1[sk1])] = S12.conj().T
+            # remove the redundant DOFs
+            red1 = p1[red[red < nI1]]
+            red2 = p2[red[red >= nI1] - nI1]
+            keep1 = np.setdiff1d(np.arange(len(self.dofs[c1])), red1)
+            self._restrict(c1, keep1, lvl)
+            keep2 = np.setdiff1d(np.arange(len(self.dofs[c2])), red2)
+            self._restrict(c2, keep2, lvl)
+        if st.blocks:
+            self.stages.append(st)
+        self.stats.append(("edge", lvl, nred, sum(len(v) for v in self.dofs.values())))
+
+    def _pos_of(self, c, ids):
+        """Positions in dofs[c] of the global DOF ids `ids` (all still active)."""
+        if ids is None or len(ids) == 0:
+            return np.zeros(0, dtype=np.int64)
+        order = np.argsort(self.dofs[c])
+        pos = order[np.searchsorted(self.dofs[c], ids, sorter=order)]
+        assert np.array_equal(self.dofs[c][pos], ids)
+        return pos
+
+    def _merge(self, lvl: int):
+        """Concatenate the active DOFs of siblings; assemble the parent level's near field."""
+        g = self.g
+        beta = g.beta
+        plvl = lvl - 1
+        dofs, near = {}, {}
+        for p in range(beta ** plvl):
+            kids = beta * p + np.arange(beta)
+            dofs[p] = np.concatenate([self.dofs[c] for c in kids])
+        for p in range(beta ** plvl):
+            kids = beta * p + np.arange(beta)
+            for p2 in g.NL[plvl][p]:
+                kids2 = beta * p2 + np.arange(beta)
+                blocks = []
+                for c in kids:
+                    row = []
+                    for c2 in kids2:
+                        if c2 in g.NL[lvl][c]:
+                            row.append(self.near[(c, c2)])
+                        else:
+                            row.append(self._lowrank_block(lvl, c, c2, self.dofs[c], self.dofs[c2]))
+                    blocks.append(row)
+                near[(p, p2)] = np.block(blocks) if dofs[p].size and dofs[p2].size else \
+                    np.zeros((len(dofs[p]), len(dofs[p2])), dtype=np.complex128)
+        self.dofs, self.near = dofs, near
+
+    def _root(self, lvl: int):
+        g = self.g
+        cells = [c for c in range(g.beta ** lvl) if len(self.dofs[c])]
+        S0 = np.concatenate([self.dofs[c] for c in cells]) if cells else np.zeros(0, dtype=np.int64)
+        rows = []
+        for c in cells:
+            row = []
+            for c2 in cells:
+                if c2 in g.NL[lvl][c]:
+                    row.append(self.near[(c, c2)])
+                else:
+                    row.append(self._far_pair(lvl, c, c2))
+            rows.append(row)
+        st = Stage(KIND_INPLACE, self.t.N, self.t.N, ROLE_ROOT, level=0)
+        if cells:
+            A0 = np.block(rows)
+            A0 = 0.5 * (A0 + A0.conj().T)
+            L = np.linalg.cholesky(A0)
+            A0inv = sla.cho_solve((L, True), np.eye(len(S0), dtype=np.complex128))
+            A0inv = 0.5 * (A0inv + A0inv.conj().T)
+            st.add(A0inv, S0, S0)
+        self.root_size = len(S0)
+        self.stages.append(st)
+
+    def _far_pair(self, lvl, c, c2):
+        """A[dofs c, dofs c2] for cells not in each other's NL at `lvl`: find the admissible level."""
+        for up in range(lvl, 0, -1):
+            a = self.g.ancestor(lvl, c, up)
+            a2 = self.g.ancestor(lvl, c2, up)
+            if a2 in self.g.IL[up][a]:
+                size = self.t.size(up)
+                return self.H.lowrank[up].get(self.t, up, a, a2,
+                                              self.t.pos[self.dofs[c]] - a * size,
+                                              self.t.pos[self.dofs[c2]] - a2 * size)
+        raise RuntimeError("cells neither near nor admissible")
+
+
+def build_hif(H: HMatrix, eps: float, **kw):
+    h = HIF(H, eps, **kw)
+    return h.run(), h
