@@ -1,0 +1,159 @@
+/*
+ * fio.h -- C ABI of libfio: GPU apply of the approximate inverse of a discrete Fourier integral
+ * operator (FIO), K^{-1} ~ G-dot K-dot*, on one NVIDIA GB300 (sm_103a).
+ *
+ * The problem (paper section 1, eq. 1.6): u = K f-hat with K_ij = a(x_i, xi_j) exp(2 pi i Phi(x_i, xi_j))
+ * on the n^d grids X = {k/n} and Omega = {-n/2 .. n/2-1}^d.  The approximate inverse (section 5,
+ * Algorithm 1) is the product of
+ *   K-dot*  the adjoint butterfly factorisation (section 2, eq. for K-dot and its adjoint):
+ *           L+3 block-sparse factors V_L H_{L-1} ... H_{L/2} D* C*_{L/2} ... C*_{L-1} U_L*;
+ *   G-dot   the hierarchical interpolative factorisation of (K*K)^{-1} (section 4, eqs. for G-dot
+ *           in 1D and 2D): R_L ... R_1 A_0^{-1} R_1* ... R_L* (2D: R_l Rbar_l pairs).
+ * The factors are built once on the host (Python builder) and handed over as one packed buffer.
+ *
+ * VECTORS.  Every vector argument is a DEVICE pointer to an N x b complex array in column-major
+ * order with leading dimension ld >= N (column j = right-hand side j), in natural grid order:
+ * 1D index i <-> x_i = i/n (X side) or xi_i = i - n/2 (Omega side); 2D index i1 + n*i2 <-> the
+ * point (i1, i2).  Complex values are interleaved (re, im): double pairs for FIO_C128, float
+ * pairs for FIO_C64 (the layouts of torch.complex128 / torch.complex64).  Inputs and outputs must
+ * not overlap.  b >= 0; b == 0 is a no-op.
+ *
+ * PRECISION.  FIO_P64 applies the FP64 (complex128) copy of the factors, FIO_P32 the FP32
+ * (complex64) copy, which fio_upload_factors derives on the device.  The vector dtype must match
+ * the precision (C128 with P64, C64 with P32); other pairs return FIO_EINVAL.
+ *
+ * STREAMS AND SCRATCH.  Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ * default stream) unless stated otherwise.  Each operator owns a scratch pool (device memory for
+ * the intermediate stage vectors) that grows on demand; growing synchronises `stream`.  Calls on
+ * the same operator must not run concurrently (they share the scratch pool): issue them on one
+ * stream.  Distinct operators are independent.
+ *
+ * ERRORS.  Every call returns an int status: FIO_OK (0) or a negative FIO_E* code; nothing is
+ * thrown and nothing aborts.  Launch errors and errors of earlier asynchronous work found at the
+ * call return FIO_ECUDA.  fio_strerror gives a static message.
+ *
+ * PACKED FACTOR BUFFER (little-endian; produced by paper_2105_02995_gb300/builder/pack.py):
+ *   header, 256 bytes:
+ *     0  char[8] magic "FIOPACK1"      8  u32 version (1)     12 u32 d (1 or 2)
+ *     16 i64 n                         24 i64 N = n^d
+ *     32 u32 n_bf   (butterfly stages, in the order they act on f-hat)
+ *     36 u32 n_hif  (HIF stages R_L*, (Rbar_L*), ..., R_1*, (Rbar_1*) in that order)
+ *     40 u32 n_root (0 or 1: the stage holding A_0^{-1})      44 u32 flags
+ *     48 f64 eps_bf                    56 f64 eps_hif
+ *     64 u64 stage_table offset        72 u64 data offset     80 u64 total bytes
+ *     88 u64 checksum = sum_k w_k (2k+1) mod 2^64 over the u64 words w_k of [data, total)
+ *   stage table: n_bf + n_hif + n_root entries of 64 bytes:
+ *     0 u32 kind (0 MAP, 1 INPLACE)  4 u32 nblk  8 u32 R  12 u32 C
+ *     16 i64 in_len  24 i64 out_len  32 u64 offset of M  40 u64 offset of in  48 u64 offset of out
+ *     56 u32 level   60 u32 role (0 butterfly, 1 HIF cell, 2 HIF edge, 3 root)
+ *   per stage: M = complex128[nblk][R][C] (row-major per block), in = int32[nblk][C],
+ *   out = int32[nblk][R]; index -1 marks padding; all offsets 256-byte aligned.
+ *   MAP stage: y = S x with y[out[b][r]] = sum_c M[b][r][c] x[in[b][c]]; its valid out indices
+ *   are a permutation of [0, out_len) and its valid in indices a permutation of [0, in_len).
+ *   INPLACE stage (R == C, in == out): x[I_b] <- M_b x[I_b] on disjoint index sets I_b, the
+ *   identity elsewhere; in_len == out_len == N.
+ *   K-dot = S_{n_bf} ... S_1;  K-dot* = S_1^* ... S_{n_bf}^*;
+ *   G-dot = H_1^* ... H_T^* A_0^{-1} H_T ... H_1 (H_t the t-th HIF stage, H_1 = R_L*).
+ */
+#ifndef FIO_H
+#define FIO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FIO_OK 0
+#define FIO_EINVAL (-1)      /* bad argument: null pointer, size, ld < N, dtype/precision pair   */
+#define FIO_ENOMEM (-2)      /* device (or pinned host) allocation failed                         */
+#define FIO_EBADFACTORS (-3) /* packed buffer damaged or inconsistent (magic, sizes, checksum,
+                                index lists)                                                      */
+#define FIO_ENOCONV (-4)     /* iterative solve stopped at maxit above the tolerance             */
+#define FIO_ETIMEOUT (-5)    /* a bounded device wait gave up                                     */
+#define FIO_ECUDA (-6)       /* a CUDA runtime call or kernel launch failed                       */
+#define FIO_ENOTSUP (-7)     /* the operator lacks the factors this call needs (e.g. no HIF)      */
+
+typedef struct fio_op_s* fio_op;
+
+typedef enum { FIO_C128 = 0, FIO_C64 = 1 } fio_dtype;
+typedef enum { FIO_P64 = 0, FIO_P32 = 1 } fio_precision;
+typedef enum { FIO_DIRECT = 0, FIO_PCG = 1, FIO_GMRES = 2, FIO_IR = 3 } fio_method;
+
+#define FIO_MASK_P64 1u
+#define FIO_MASK_P32 2u
+
+typedef struct {
+  int method;    /* fio_method                                                                 */
+  int inner;     /* fio_precision of the preconditioner / inner correction (FIO_IR: P32 or P64) */
+  double tol;    /* stop when ||u - K-dot f|| <= tol ||u|| for every right-hand side           */
+  int maxit;     /* iteration cap (outer iterations for FIO_IR)                                 */
+  int restart;   /* GMRES restart length (FIO_GMRES, and the inner GMRES of FIO_IR)             */
+} fio_solve_opts;
+
+typedef struct {
+  int iters;     /* iterations taken                                                            */
+  double relres; /* final ||u - K-dot f|| / ||u||                                               */
+  int status;    /* FIO_OK or FIO_ENOCONV                                                       */
+} fio_solve_info;
+
+/* Validate `packed` (nbytes host bytes; the layout above), copy it to the device of the current
+ * CUDA context and derive the precision copies named by precisions_mask (FIO_MASK_P64 and/or
+ * FIO_MASK_P32; 0 means both).  The caller keeps ownership of `packed` and may free it on return
+ * (the copy is synchronous with respect to the host).  On success *out owns the device copies
+ * until fio_release.  Errors: FIO_EINVAL (null args), FIO_EBADFACTORS, FIO_ENOMEM, FIO_ECUDA. */
+int fio_upload_factors(const void* packed, size_t nbytes, unsigned precisions_mask, void* stream,
+                       fio_op* out);
+
+/* y = K-dot x: the butterfly factors (section 2, eq. for K-dot), x on Omega, y on X. */
+int fio_apply_K(fio_op op, const void* x, void* y, int64_t ld, int b, int dtype, int precision,
+                void* stream);
+
+/* y = K-dot* x: conjugate-transposed butterfly factors in reverse order, x on X, y on Omega. */
+int fio_apply_Kadj(fio_op op, const void* x, void* y, int64_t ld, int b, int dtype, int precision,
+                   void* stream);
+
+/* y = G-dot x ~ (K*K)^{-1} x (section 4, eqs. for G-dot); needs the HIF stages (else ENOTSUP). */
+int fio_apply_G(fio_op op, const void* x, void* y, int64_t ld, int b, int dtype, int precision,
+                void* stream);
+
+/* f = G-dot K-dot* u ~ K^{-1} u: the direct solver (section 5).  u on X, f on Omega. */
+int fio_apply_inv(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype, int precision,
+                  void* stream);
+
+/* As fio_apply_inv, but u and f are HOST pointers (pageable or pinned): the call copies u to the
+ * device, applies, copies f back and synchronises `stream` before returning. */
+int fio_apply_inv_host(fio_op op, const void* u_host, void* f_host, int64_t ld, int b, int dtype,
+                       int precision, void* stream);
+
+/* Iterative solve of K-dot f = u to ||u - K-dot f|| <= tol ||u|| (section 5, eq. for the CG system):
+ *   FIO_DIRECT  f = G-dot K-dot* u (no iteration);
+ *   FIO_PCG     CG on K-dot* K-dot f = K-dot* u preconditioned with G-dot (the paper's solver);
+ *   FIO_GMRES   GMRES on K-dot f = u right-preconditioned with G-dot K-dot*;
+ *   FIO_IR      iterative refinement: FP64 residual r = u - K-dot f, correction G-dot K-dot* r in
+ *               opts->inner precision, FP64 update f += d.
+ * f holds the initial guess on entry (zero it for none) and the solution on return.  dtype must
+ * be FIO_C128 (FP64 solution).  info_host (may be NULL) receives one record per right-hand side;
+ * the call synchronises `stream`.  Returns FIO_OK, FIO_ENOCONV, or an error code. */
+int fio_solve(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
+              const fio_solve_opts* opts, fio_solve_info* info_host, void* stream);
+
+/* Operator facts: dimension, grid size n, N = n^d, device bytes held (factors + scratch). */
+int fio_query(fio_op op, int* d, int64_t* n, int64_t* N, size_t* device_bytes);
+
+/* Stage counts and the number of kernel launches one apply issues (for launch accounting):
+ * which = 0 apply_K, 1 apply_Kadj, 2 apply_G, 3 apply_inv. */
+int fio_launch_count(fio_op op, int which, int b, int* launches);
+
+/* Free the device copies and scratch of op (synchronises the device first).  NULL is a no-op. */
+int fio_release(fio_op op);
+
+/* Static, NUL-terminated description of a status code. */
+const char* fio_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIO_H */

@@ -1,0 +1,247 @@
+"""ctypes binding of libfio (include/fio.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module checks shapes and dtypes, passes
+pointers, sizes and the current torch stream, and turns status codes into exceptions.  It never
+computes anything itself and has no CPU fallback: ``load()`` raises when libfio.so is missing.
+
+Vectors are torch tensors on the GPU of shape (N,) or (N, b), column-major (stride (1, ld)),
+complex128 (FP64 path) or complex64 (FP32 path).  ``colmajor`` makes such a tensor.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfio.so")
+
+FIO_C128, FIO_C64 = 0, 1
+FIO_P64, FIO_P32 = 0, 1
+FIO_DIRECT, FIO_PCG, FIO_GMRES, FIO_IR = 0, 1, 2, 3
+FIO_MASK_P64, FIO_MASK_P32 = 1, 2
+STATUS = {0: "FIO_OK", -1: "FIO_EINVAL", -2: "FIO_ENOMEM", -3: "FIO_EBADFACTORS",
+          -4: "FIO_ENOCONV", -5: "FIO_ETIMEOUT", -6: "FIO_ECUDA", -7: "FIO_ENOTSUP"}
+SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv",
+           "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_release",
+           "fio_strerror"]
+
+_lib = None
+
+
+class FioError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({_lib.fio_strerror(status).decode() if _lib else ''})")
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("inner", ctypes.c_int), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("restart", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("relres", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+def load(path: str = LIB_PATH):
+    """Load libfio.so (raises OSError when it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libfio.so not found at {path}; run paper_2105_02995_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.fio_upload_factors.argtypes = [vp, ctypes.c_size_t, ctypes.c_uint, vp, ctypes.POINTER(vp)]
+    for name in ("fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv", "fio_apply_inv_host"):
+        getattr(lib, name).argtypes = [vp, vp, vp, i64, c_int, c_int, c_int, vp]
+    lib.fio_solve.argtypes = [vp, vp, vp, i64, c_int, c_int, ctypes.POINTER(SolveOpts),
+                              ctypes.POINTER(SolveInfo), vp]
+    lib.fio_query.argtypes = [vp, ctypes.POINTER(c_int), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                              ctypes.POINTER(ctypes.c_size_t)]
+    lib.fio_launch_count.argtypes = [vp, c_int, c_int, ctypes.POINTER(c_int)]
+    lib.fio_release.argtypes = [vp]
+    lib.fio_strerror.argtypes = [c_int]
+    lib.fio_strerror.restype = ctypes.c_char_p
+    for name in SYMBOLS:
+        if name != "fio_strerror":
+            getattr(lib, name).restype = c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise FioError(rc, what)
+
+
+def colmajor(t):
+    """A column-major copy of a (N, b) torch tensor (or the tensor itself if it already is)."""
+    if t.dim() == 1 or (t.stride(0) == 1 and t.stride(1) >= t.shape[0]):
+        return t
+    return t.t().contiguous().t()
+
+
+def _vec(t, N):
+    import torch
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype == torch.complex128:
+        dtype, prec = FIO_C128, FIO_P64
+    elif t.dtype == torch.complex64:
+        dtype, prec = FIO_C64, FIO_P32
+    else:
+        raise ValueError(f"unsupported dtype {t.dtype}")
+    if t.dim() == 1:
+        if t.shape[0] != N or t.stride(0) != 1:
+            raise ValueError("vector must have N contiguous entries")
+        return dtype, prec, 1, N
+    if t.shape[0] != N or t.stride(0) != 1:
+        raise ValueError("expected an N x b column-major tensor (stride (1, ld))")
+    return dtype, prec, t.shape[1], max(t.stride(1), N)
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Operator:
+    """A packed operator uploaded to the current CUDA device (fio_upload_factors)."""
+
+    def __init__(self, packed: bytes, precisions: int = 0):
+        lib = load()
+        self._lib = lib
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(packed, len(packed))
+        _check(lib.fio_upload_factors(buf, len(packed), precisions, _stream(), ctypes.byref(h)),
+               "fio_upload_factors")
+        self.h = h
+        d, n, N, nb = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        _check(lib.fio_query(h, ctypes.byref(d), ctypes.byref(n), ctypes.byref(N), ctypes.byref(nb)), "fio_query")
+        self.d, self.n, self.N = d.value, n.value, N.value
+
+    def device_bytes(self) -> int:
+        nb = ctypes.c_size_t()
+        _check(self._lib.fio_query(self.h, None, None, None, ctypes.byref(nb)), "fio_query")
+        return nb.value
+
+    def launches(self, which: str, b: int) -> int:
+        k = {"K": 0, "Kadj": 1, "G": 2, "inv": 3}[which]
+        out = ctypes.c_int()
+        _check(self._lib.fio_launch_count(self.h, k, b, ctypes.byref(out)), "fio_launch_count")
+        return out.value
+
+    def _apply(self, fn, name, x, y):
+        import torch
+        if y is None:
+            y = torch.empty_like(colmajor(x) if x.dim() == 2 else x)
+            y = colmajor(y) if y.dim() == 2 else y
+        dt, prec, b, ld = _vec(x, self.N)
+        dty, precy, by, ldy = _vec(y, self.N)
+        if (dt, b) != (dty, by) or ld != ldy:
+            raise ValueError("x and y must have the same dtype, shape and leading dimension")
+        _check(fn(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), ld, b, dt,
+                  prec, _stream()), name)
+        return y
+
+    def apply_K(self, x, y=None):
+        return self._apply(self._lib.fio_apply_K, "fio_apply_K", x, y)
+
+    def apply_Kadj(self, x, y=None):
+        return self._apply(self._lib.fio_apply_Kadj, "fio_apply_Kadj", x, y)
+
+    def apply_G(self, x, y=None):
+        return self._apply(self._lib.fio_apply_G, "fio_apply_G", x, y)
+
+    def apply_inv(self, u, f=None):
+        return self._apply(self._lib.fio_apply_inv, "fio_apply_inv", u, f)
+
+    def apply_inv_host(self, u: np.ndarray, f: np.ndarray | None = None) -> np.ndarray:
+        """Host-buffer direct solve: numpy (N, b) Fortran-ordered complex128/complex64 arrays."""
+        u = np.asfortranarray(u)
+        if u.ndim == 1:
+            u = u[:, None]
+        if f is None:
+            f = np.empty_like(u, order="F")
+        if u.dtype == np.complex128:
+            dt, prec = FIO_C128, FIO_P64
+        elif u.dtype == np.complex64:
+            dt, prec = FIO_C64, FIO_P32
+        else:
+            raise ValueError("complex128 or complex64 expected")
+        if u.shape[0] != self.N or f.shape != u.shape or f.dtype != u.dtype or not f.flags.f_contiguous:
+            raise ValueError("bad host arrays")
+        _check(self._lib.fio_apply_inv_host(self.h, u.ctypes.data_as(ctypes.c_void_p),
+                                            f.ctypes.data_as(ctypes.c_void_p), self.N, u.shape[1],
+                                            dt, prec, _stream()), "fio_apply_inv_host")
+        return f
+
+    def solve(self, u, f=None, method: int = FIO_GMRES, inner: int = FIO_P64, tol: float = 1e-10,
+              maxit: int = 100, restart: int = 20):
+        """Iterative solve of K-dot f = u (complex128 tensors); returns (f, list of (iters, relres, status))."""
+        import torch
+        if f is None:
+            f = torch.zeros_like(u)
+        dt, prec, b, ld = _vec(u, self.N)
+        if dt != FIO_C128:
+            raise ValueError("fio_solve takes complex128 vectors")
+        opts = SolveOpts(method, inner, tol, maxit, restart)
+        infos = (SolveInfo * max(b, 1))()
+        rc = self._lib.fio_solve(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(f.data_ptr()),
+                                 ld, b, dt, ctypes.byref(opts), infos, _stream())
+        if rc not in (0, -4):
+            _check(rc, "fio_solve")
+        return f, [(infos[j].iters, infos[j].relres, infos[j].status) for j in range(b)]
+
+    def release(self):
+        if getattr(self, "h", None):
+            self._lib.fio_release(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class NormalMatvecGPU:
+    """K-dot* K-dot X on the GPU for the builder's peeling probes (bind() takes the butterfly
+    stages and uploads them as a butterfly-only operator)."""
+
+    def __init__(self, precision: int = FIO_P64, chunk: int = 256):
+        self.precision = precision
+        self.chunk = chunk
+
+    def bind(self, bf_stages):
+        from .builder.pack import pack
+        st0 = bf_stages[0]
+        N = st0.in_len
+        d = 1
+        n = N
+        r = int(round(N ** 0.5))
+        if getattr(self, "d", None) == 2 or (hasattr(self, "grid") and self.grid == 2):
+            d, n = 2, r
+        packed = pack(d, n, bf_stages, [], [], 0.0, 0.0)
+        op = Operator(packed)
+        prec = self.precision
+        chunk = self.chunk
+
+        def mv(X):
+            import torch
+            X = np.asarray(X)
+            out = np.empty((X.shape[0], X.shape[1]), dtype=np.complex128)
+            dt = torch.complex128 if prec == FIO_P64 else torch.complex64
+            for s in range(0, X.shape[1], chunk):
+                xb = torch.from_numpy(np.ascontiguousarray(X[:, s:s + chunk].T)).to("cuda", dt).t()
+                yb = op.apply_K(xb)
+                zb = op.apply_Kadj(yb)
+                out[:, s:s + chunk] = zb.t().cpu().numpy().T
+            return out
+
+        mv.op = op
+        return mv

@@ -1,0 +1,479 @@
+// fio_capi.cu -- the C ABI of include/fio.h: upload of the packed factors, the applies of
+// K-dot (paper section 2), K-dot* , G-dot (section 4) and G-dot K-dot* (section 5), and the
+// operator bookkeeping.  The iterative solvers live in fio_solve.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "fio.h"
+#include "fio_internal.h"
+#include "fio_kernels.cuh"
+
+using namespace fio;
+
+namespace {
+
+constexpr size_t kHeader = 256;
+constexpr size_t kStageBytes = 64;
+
+template <typename T>
+T rd(const uint8_t* p, size_t off) {
+  T v;
+  memcpy(&v, p + off, sizeof(T));
+  return v;
+}
+
+uint64_t checksum(const uint8_t* p, size_t start, size_t end) {
+  uint64_t s = 0;
+  const size_t nw = (end - start) / 8;
+  for (size_t k = 0; k < nw; ++k) {
+    uint64_t w;
+    memcpy(&w, p + start + 8 * k, 8);
+    s += w * (2 * (uint64_t)k + 1);
+  }
+  return s;
+}
+
+// every valid index of `idx` in [0, len) and each value of [0, len) exactly once
+bool is_permutation(const int32_t* idx, size_t n, int64_t len) {
+  std::vector<uint8_t> seen((size_t)len, 0);
+  int64_t cnt = 0;
+  for (size_t k = 0; k < n; ++k) {
+    const int32_t v = idx[k];
+    if (v < 0) continue;
+    if (v >= len || seen[v]) return false;
+    seen[v] = 1;
+    ++cnt;
+  }
+  return cnt == len;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// upload
+// ---------------------------------------------------------------------------------------------
+extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned mask, void* stream,
+                                  fio_op* out) {
+  if (!packed || !out) return FIO_EINVAL;
+  *out = nullptr;
+  if (mask == 0) mask = FIO_MASK_P64 | FIO_MASK_P32;
+  const uint8_t* p = (const uint8_t*)packed;
+  if (nbytes < kHeader || memcmp(p, "FIOPACK1", 8) != 0) return FIO_EBADFACTORS;
+  const uint32_t version = rd<uint32_t>(p, 8), d = rd<uint32_t>(p, 12);
+  const int64_t n = rd<int64_t>(p, 16), N = rd<int64_t>(p, 24);
+  const uint32_t n_bf = rd<uint32_t>(p, 32), n_hif = rd<uint32_t>(p, 36), n_root = rd<uint32_t>(p, 40);
+  const uint64_t tab = rd<uint64_t>(p, 64), data = rd<uint64_t>(p, 72), total = rd<uint64_t>(p, 80),
+                 csum = rd<uint64_t>(p, 88);
+  if (version != 1 || (d != 1 && d != 2) || n <= 0 || N <= 0 || N > (int64_t)1 << 31) return FIO_EBADFACTORS;
+  if ((d == 1 && N != n) || (d == 2 && N != n * n)) return FIO_EBADFACTORS;
+  if (total != nbytes || data > total || (total - data) % 8 || n_root > 1 || n_bf == 0) return FIO_EBADFACTORS;
+  const uint64_t nst = (uint64_t)n_bf + n_hif + n_root;
+  if (tab < kHeader || tab + nst * kStageBytes > data) return FIO_EBADFACTORS;
+  if (checksum(p, data, total) != csum) return FIO_EBADFACTORS;
+
+  fio_op_s* op = new (std::nothrow) fio_op_s();
+  if (!op) return FIO_ENOMEM;
+  op->d = (int)d;
+  op->n = n;
+  op->N = N;
+  op->n_bf = (int)n_bf;
+  op->n_hif = (int)n_hif;
+  op->n_root = (int)n_root;
+  op->mask = mask;
+  op->max_len = N;
+  size_t m_elems = 0;
+  int64_t prev_out = N;
+  for (uint64_t s = 0; s < nst; ++s) {
+    const size_t e = tab + s * kStageBytes;
+    Stage st{};
+    st.kind = rd<uint32_t>(p, e);
+    st.nblk = rd<uint32_t>(p, e + 4);
+    st.R = rd<uint32_t>(p, e + 8);
+    st.C = rd<uint32_t>(p, e + 12);
+    st.in_len = rd<int64_t>(p, e + 16);
+    st.out_len = rd<int64_t>(p, e + 24);
+    st.offM = rd<uint64_t>(p, e + 32);
+    st.offIn = rd<uint64_t>(p, e + 40);
+    st.offOut = rd<uint64_t>(p, e + 48);
+    st.level = rd<uint32_t>(p, e + 56);
+    st.role = rd<uint32_t>(p, e + 60);
+    const uint64_t mb = (uint64_t)st.nblk * st.R * st.C * 16, ib = (uint64_t)st.nblk * st.C * 4,
+                   ob = (uint64_t)st.nblk * st.R * 4;
+    const bool bf = s < n_bf;
+    bool ok = st.kind <= 1 && st.offM % 16 == 0 && st.offIn % 4 == 0 && st.offOut % 4 == 0 &&
+              st.offM >= data && st.offIn >= data && st.offOut >= data && st.offM + mb <= total &&
+              st.offIn + ib <= total && st.offOut + ob <= total && st.in_len > 0 && st.out_len > 0 &&
+              st.in_len < ((int64_t)1 << 31) && st.out_len < ((int64_t)1 << 31) &&
+              (st.nblk == 0 || (st.R > 0 && st.C > 0));
+    if (ok && bf) {
+      ok = st.kind == 0 && st.in_len == prev_out &&
+           is_permutation((const int32_t*)(p + st.offIn), (size_t)st.nblk * st.C, st.in_len) &&
+           is_permutation((const int32_t*)(p + st.offOut), (size_t)st.nblk * st.R, st.out_len);
+      prev_out = st.out_len;
+      if (st.out_len > op->max_len) op->max_len = st.out_len;
+      if (s + 1 == n_bf && st.out_len != N) ok = false;
+    } else if (ok) {
+      // INPLACE: square blocks, identical in/out lists, disjoint index sets inside [0, N)
+      ok = st.kind == 1 && st.R == st.C && st.in_len == N && st.out_len == N &&
+           memcmp(p + st.offIn, p + st.offOut, ib) == 0;
+      if (ok) {
+        std::vector<uint8_t> seen((size_t)N, 0);
+        const int32_t* ii = (const int32_t*)(p + st.offIn);
+        for (size_t k = 0; ok && k < (size_t)st.nblk * st.C; ++k) {
+          const int32_t v = ii[k];
+          if (v < 0) continue;
+          if (v >= N || seen[v]) ok = false;
+          else seen[v] = 1;
+        }
+      }
+    }
+    if (!ok) {
+      delete op;
+      return FIO_EBADFACTORS;
+    }
+    st.launch_rows = 0;
+    m_elems += (size_t)st.nblk * st.R * st.C;
+    op->st.push_back(st);
+  }
+
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMalloc(&op->arena, nbytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete op;
+    return FIO_ENOMEM;
+  }
+  op->arena_bytes = nbytes;
+  if (cudaMemcpyAsync(op->arena, packed, nbytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    fio_release(op);
+    return FIO_ECUDA;
+  }
+  if (mask & FIO_MASK_P32) {
+    if (cudaMalloc(&op->arena32, m_elems * sizeof(float2) + 256) != cudaSuccess) {
+      cudaGetLastError();
+      fio_release(op);
+      return FIO_ENOMEM;
+    }
+    op->arena32_bytes = m_elems * sizeof(float2) + 256;
+  }
+  size_t off32 = 0;
+  for (auto& st : op->st) {
+    const size_t ne = (size_t)st.nblk * st.R * st.C;
+    st.M64 = (const double2*)((const uint8_t*)op->arena + st.offM);
+    st.in = (const int*)((const uint8_t*)op->arena + st.offIn);
+    st.out = (const int*)((const uint8_t*)op->arena + st.offOut);
+    if (op->arena32) {
+      float2* dst = (float2*)op->arena32 + off32;
+      st.M32 = dst;
+      if (ne) {
+        k_cast_c128_c64<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(st.M64, dst, ne);
+      }
+      off32 += ne;
+    }
+  }
+  if (!(mask & FIO_MASK_P64)) {
+    // keep the FP64 copy anyway: the index lists live in the same arena
+  }
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    fio_release(op);
+    return FIO_ECUDA;
+  }
+  *out = op;
+  return FIO_OK;
+}
+
+extern "C" int fio_release(fio_op op) {
+  if (!op) return FIO_OK;
+  cudaDeviceSynchronize();
+  if (op->arena) cudaFree(op->arena);
+  if (op->arena32) cudaFree(op->arena32);
+  if (op->scratch) cudaFree(op->scratch);
+  fio_solver_free(op);
+  cudaGetLastError();
+  delete op;
+  return FIO_OK;
+}
+
+extern "C" int fio_query(fio_op op, int* d, int64_t* n, int64_t* N, size_t* device_bytes) {
+  if (!op) return FIO_EINVAL;
+  if (d) *d = op->d;
+  if (n) *n = op->n;
+  if (N) *N = op->N;
+  if (device_bytes) *device_bytes = op->arena_bytes + op->arena32_bytes + op->scratch_bytes + op->solver_bytes;
+  return FIO_OK;
+}
+
+extern "C" const char* fio_strerror(int status) {
+  switch (status) {
+    case FIO_OK: return "ok";
+    case FIO_EINVAL: return "invalid argument";
+    case FIO_ENOMEM: return "out of device memory";
+    case FIO_EBADFACTORS: return "packed factor buffer is damaged or inconsistent";
+    case FIO_ENOCONV: return "iterative solve did not reach the tolerance";
+    case FIO_ETIMEOUT: return "bounded device wait timed out";
+    case FIO_ECUDA: return "CUDA runtime error";
+    case FIO_ENOTSUP: return "operator lacks the factors this call needs";
+    default: return "unknown status";
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// scratch pool: 5 work arrays of max(max_len, N) x b complex elements each
+// ---------------------------------------------------------------------------------------------
+int fio_scratch(fio_op op, int b, size_t elem, cudaStream_t s, void** bufs) {
+  const size_t per = (size_t)op->max_len * (size_t)b * elem;
+  const size_t per_al = (per + 255) & ~(size_t)255;
+  const size_t need = 5 * per_al;
+  if (need > op->scratch_bytes) {
+    if (op->scratch) {
+      if (cudaStreamSynchronize(s) != cudaSuccess) return FIO_ECUDA;
+      cudaFree(op->scratch);
+      op->scratch = nullptr;
+      op->scratch_bytes = 0;
+    }
+    if (cudaMalloc(&op->scratch, need) != cudaSuccess) {
+      cudaGetLastError();
+      return FIO_ENOMEM;
+    }
+    op->scratch_bytes = need;
+  }
+  for (int k = 0; k < 5; ++k) bufs[k] = (uint8_t*)op->scratch + k * per_al;
+  return FIO_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// stage launches
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+template <typename V> const V* stage_M(const Stage& st);
+template <> const double2* stage_M<double2>(const Stage& st) { return st.M64; }
+template <> const float2* stage_M<float2>(const Stage& st) { return st.M32; }
+
+template <typename V> struct ChunkK;
+template <> struct ChunkK<double2> { static constexpr int v = 16; };
+template <> struct ChunkK<float2> { static constexpr int v = 32; };
+
+template <typename V, bool ADJ, int TX, int TB, int TR>
+void launch_mm(StageArgs<V> a, cudaStream_t s) {
+  constexpr int RT = (256 / TX) * TR, BT = TX * TB;
+  const int nrows = ADJ ? a.C : a.R;
+  a.ntiles = (nrows + RT - 1) / RT;
+  dim3 grid((unsigned)(a.nblk * a.ntiles), (unsigned)((a.b + BT - 1) / BT));
+  k_stage_mm<V, ADJ, TX, TB, TR, ChunkK<V>::v><<<grid, 256, 0, s>>>(a);
+}
+
+template <typename V, bool ADJ>
+void launch_stage_dir(const StageArgs<V>& a, cudaStream_t s) {
+  if (a.b <= 4) {
+    if (!ADJ) {
+      const long long warps = (long long)a.nblk * a.R;
+      k_stage_mv_fwd<V><<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(a);
+    } else {
+      int threads = a.C < 256 ? ((a.C + 31) / 32) * 32 : 256;
+      dim3 grid((unsigned)((a.C + threads - 1) / threads), (unsigned)a.nblk);
+      k_stage_mv_adj<V><<<grid, threads, 0, s>>>(a);
+    }
+  } else if (a.b <= 8) {
+    launch_mm<V, ADJ, 8, 1, 2>(a, s);
+  } else if (a.b <= 16) {
+    launch_mm<V, ADJ, 16, 1, 4>(a, s);
+  } else {
+    launch_mm<V, ADJ, 16, 2, 4>(a, s);
+  }
+}
+
+template <typename V>
+void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long long xcs, V* y,
+                  long long yrs, long long ycs, int b, cudaStream_t s) {
+  if (st.nblk == 0) return;
+  StageArgs<V> a;
+  a.M = stage_M<V>(st);
+  a.in = st.in;
+  a.out = st.out;
+  a.nblk = (int)st.nblk;
+  a.R = (int)st.R;
+  a.C = (int)st.C;
+  a.x = x;
+  a.xrs = xrs;
+  a.xcs = xcs;
+  a.y = y;
+  a.yrs = yrs;
+  a.ycs = ycs;
+  a.b = b;
+  a.ntiles = 1;
+  if (adj) launch_stage_dir<V, true>(a, s);
+  else launch_stage_dir<V, false>(a, s);
+}
+
+// one INPLACE stage on the row-major work vector W (scratch S has the same shape)
+template <typename V>
+void inplace_stage(const Stage& st, bool adj, V* W, V* S, int b, cudaStream_t s) {
+  if (st.nblk == 0) return;
+  launch_stage<V>(st, adj, W, b, 1, S, b, 1, b, s);
+  const long long nidx = (long long)st.nblk * st.R;
+  const long long tot = nidx * b;
+  k_scatter_back<V><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(st.out, nidx, S, W, b);
+}
+
+// K-dot (adj = false) or K-dot* (adj = true): x (xrs, xcs) -> y (yrs, ycs); A, B ping-pong
+template <typename V>
+void bf_chain(fio_op op, bool adj, const V* x, long long xrs, long long xcs, V* y, long long yrs,
+              long long ycs, int b, V* A, V* B, cudaStream_t s) {
+  const int n = op->n_bf;
+  const V* cur = x;
+  long long crs = xrs, ccs = xcs;
+  for (int k = 0; k < n; ++k) {
+    const Stage& st = op->st[adj ? n - 1 - k : k];
+    const bool last = k == n - 1;
+    V* dst = last ? y : ((k & 1) ? B : A);
+    const long long drs = last ? yrs : b, dcs = last ? ycs : 1;
+    launch_stage<V>(st, adj, cur, crs, ccs, dst, drs, dcs, b, s);
+    cur = dst;
+    crs = drs;
+    ccs = dcs;
+  }
+}
+
+// G-dot on the row-major work vector W in place; S scratch
+template <typename V>
+void g_sweep(fio_op op, V* W, V* S, int b, cudaStream_t s) {
+  const int h0 = op->n_bf, nh = op->n_hif;
+  for (int t = 0; t < nh; ++t) inplace_stage<V>(op->st[h0 + t], false, W, S, b, s);
+  for (int t = 0; t < op->n_root; ++t) inplace_stage<V>(op->st[h0 + nh + t], false, W, S, b, s);
+  for (int t = nh - 1; t >= 0; --t) inplace_stage<V>(op->st[h0 + t], true, W, S, b, s);
+}
+
+template <typename V>
+void to_row(const V* X, long long ld, V* W, long long N, int b, cudaStream_t s) {
+  dim3 grid((unsigned)((N + 31) / 32), (unsigned)((b + 31) / 32));
+  k_col_to_row<V><<<grid, dim3(32, 8), 0, s>>>(X, ld, W, N, b);
+}
+template <typename V>
+void to_col(const V* W, V* Y, long long ld, long long N, int b, cudaStream_t s) {
+  dim3 grid((unsigned)((N + 31) / 32), (unsigned)((b + 31) / 32));
+  k_row_to_col<V><<<grid, dim3(32, 8), 0, s>>>(W, Y, ld, N, b);
+}
+
+int check_args(fio_op op, const void* x, const void* y, int64_t ld, int b, int dtype, int prec) {
+  if (!op || b < 0) return FIO_EINVAL;
+  if (b > 0 && (!x || !y || x == y)) return FIO_EINVAL;
+  if (ld < op->N) return FIO_EINVAL;
+  if (!((dtype == FIO_C128 && prec == FIO_P64) || (dtype == FIO_C64 && prec == FIO_P32))) return FIO_EINVAL;
+  if (prec == FIO_P32 && !op->arena32) return FIO_EINVAL;
+  const size_t es = dtype == FIO_C128 ? 16 : 8;
+  const uint8_t *xb = (const uint8_t*)x, *yb = (const uint8_t*)y;
+  const size_t span = ((size_t)ld * (b > 0 ? b - 1 : 0) + op->N) * es;
+  if (b > 0 && xb < yb + span && yb < xb + span) return FIO_EINVAL;  // overlap
+  return FIO_OK;
+}
+
+int finish(cudaStream_t) { return cudaGetLastError() == cudaSuccess ? FIO_OK : FIO_ECUDA; }
+
+enum Which { W_K = 0, W_KADJ = 1, W_G = 2, W_INV = 3 };
+
+template <typename V>
+int apply_t(fio_op op, Which w, const void* xv, void* yv, int64_t ld, int b, cudaStream_t s) {
+  void* bufs[5];
+  int rc = fio_scratch(op, b, sizeof(V), s, bufs);
+  if (rc) return rc;
+  V *A = (V*)bufs[0], *B = (V*)bufs[1], *W = (V*)bufs[2];
+  const V* x = (const V*)xv;
+  V* y = (V*)yv;
+  switch (w) {
+    case W_K: bf_chain<V>(op, false, x, 1, ld, y, 1, ld, b, A, B, s); break;
+    case W_KADJ: bf_chain<V>(op, true, x, 1, ld, y, 1, ld, b, A, B, s); break;
+    case W_G:
+      to_row<V>(x, ld, W, op->N, b, s);
+      g_sweep<V>(op, W, A, b, s);
+      to_col<V>(W, y, ld, op->N, b, s);
+      break;
+    case W_INV:
+      bf_chain<V>(op, true, x, 1, ld, W, b, 1, b, A, B, s);
+      g_sweep<V>(op, W, A, b, s);
+      to_col<V>(W, y, ld, op->N, b, s);
+      break;
+  }
+  return finish(s);
+}
+
+int apply_any(fio_op op, Which w, const void* x, void* y, int64_t ld, int b, int dtype, int prec,
+              void* stream) {
+  int rc = check_args(op, x, y, ld, b, dtype, prec);
+  if (rc) return rc;
+  if ((w == W_G || w == W_INV) && op->n_root == 0) return FIO_ENOTSUP;
+  if (b == 0) return FIO_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaGetLastError() != cudaSuccess) return FIO_ECUDA;
+  return prec == FIO_P64 ? apply_t<double2>(op, w, x, y, ld, b, s)
+                         : apply_t<float2>(op, w, x, y, ld, b, s);
+}
+
+}  // namespace
+
+// internal entry used by the solvers (same semantics as the public applies)
+int fio_apply_internal(fio_op op, int which, const void* x, void* y, int64_t ld, int b, int prec,
+                       cudaStream_t s) {
+  if (b == 0) return FIO_OK;
+  return prec == FIO_P64 ? apply_t<double2>(op, (Which)which, x, y, ld, b, s)
+                         : apply_t<float2>(op, (Which)which, x, y, ld, b, s);
+}
+
+extern "C" int fio_apply_K(fio_op op, const void* x, void* y, int64_t ld, int b, int dtype,
+                           int precision, void* stream) {
+  return apply_any(op, W_K, x, y, ld, b, dtype, precision, stream);
+}
+extern "C" int fio_apply_Kadj(fio_op op, const void* x, void* y, int64_t ld, int b, int dtype,
+                              int precision, void* stream) {
+  return apply_any(op, W_KADJ, x, y, ld, b, dtype, precision, stream);
+}
+extern "C" int fio_apply_G(fio_op op, const void* x, void* y, int64_t ld, int b, int dtype,
+                           int precision, void* stream) {
+  return apply_any(op, W_G, x, y, ld, b, dtype, precision, stream);
+}
+extern "C" int fio_apply_inv(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
+                             int precision, void* stream) {
+  return apply_any(op, W_INV, u, f, ld, b, dtype, precision, stream);
+}
+
+extern "C" int fio_apply_inv_host(fio_op op, const void* u_host, void* f_host, int64_t ld, int b,
+                                  int dtype, int precision, void* stream) {
+  if (!op || !u_host || !f_host || b < 0 || ld < op->N) return FIO_EINVAL;
+  if (!((dtype == FIO_C128 && precision == FIO_P64) || (dtype == FIO_C64 && precision == FIO_P32)))
+    return FIO_EINVAL;
+  if (op->n_root == 0) return FIO_ENOTSUP;
+  if (b == 0) return FIO_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t es = dtype == FIO_C128 ? 16 : 8;
+  void* bufs[5];
+  int rc = fio_scratch(op, b, es, s, bufs);
+  if (rc) return rc;
+  void *U = bufs[3], *F = bufs[4];
+  const size_t w = (size_t)op->N * es;
+  if (cudaMemcpy2DAsync(U, w, u_host, (size_t)ld * es, w, (size_t)b, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return FIO_ECUDA;
+  rc = fio_apply_internal(op, W_INV, U, F, op->N, b, precision, s);
+  if (rc) return rc;
+  if (cudaMemcpy2DAsync(f_host, (size_t)ld * es, F, w, w, (size_t)b, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return FIO_ECUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? FIO_OK : FIO_ECUDA;
+}
+
+extern "C" int fio_launch_count(fio_op op, int which, int b, int* launches) {
+  if (!op || !launches || which < 0 || which > 3) return FIO_EINVAL;
+  int bfl = 0, gl = 0;
+  for (int k = 0; k < op->n_bf; ++k) bfl += op->st[k].nblk ? 1 : 0;
+  for (int k = op->n_bf; k < op->n_bf + op->n_hif; ++k) gl += op->st[k].nblk ? 4 : 0;
+  for (int k = op->n_bf + op->n_hif; k < (int)op->st.size(); ++k) gl += op->st[k].nblk ? 2 : 0;
+  switch (which) {
+    case 0:
+    case 1: *launches = b ? bfl : 0; break;
+    case 2: *launches = b ? gl + 2 : 0; break;
+    case 3: *launches = b ? bfl + gl + 1 : 0; break;
+  }
+  return FIO_OK;
+}

@@ -1,0 +1,49 @@
+// fio_internal.h -- operator object shared by the translation units of libfio (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "fio.h"
+
+namespace fio {
+
+struct Stage {
+  uint32_t kind, nblk, R, C;
+  int64_t in_len, out_len;
+  uint64_t offM, offIn, offOut;
+  uint32_t level, role;
+  const double2* M64 = nullptr;  // device, complex128 blocks (inside the arena)
+  const float2* M32 = nullptr;   // device, complex64 copy (inside arena32)
+  const int* in = nullptr;       // device
+  const int* out = nullptr;      // device
+  long long launch_rows;
+};
+
+}  // namespace fio
+
+struct fio_op_s {
+  int d = 0;
+  int64_t n = 0, N = 0;
+  int n_bf = 0, n_hif = 0, n_root = 0;
+  unsigned mask = 0;
+  int64_t max_len = 0;            // longest vector between two stages (>= N)
+  std::vector<fio::Stage> st;     // butterfly stages, HIF stages, root
+  void* arena = nullptr;          // device copy of the packed buffer
+  size_t arena_bytes = 0;
+  void* arena32 = nullptr;        // complex64 copies of every stage's blocks
+  size_t arena32_bytes = 0;
+  void* scratch = nullptr;        // 5 work arrays of max_len x b (grown on demand)
+  size_t scratch_bytes = 0;
+  void* solver = nullptr;         // solver work arrays (fio_solve.cu)
+  size_t solver_bytes = 0;
+};
+
+// scratch work arrays (5 of max_len x b elements of `elem` bytes); grows with a stream sync
+int fio_scratch(fio_op op, int b, size_t elem, cudaStream_t s, void** bufs);
+// which: 0 K-dot, 1 K-dot*, 2 G-dot, 3 G-dot K-dot*; x, y column-major with leading dimension ld
+int fio_apply_internal(fio_op op, int which, const void* x, void* y, int64_t ld, int b, int prec,
+                       cudaStream_t s);
+void fio_solver_free(fio_op op);

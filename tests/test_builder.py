@@ -1,0 +1,103 @@
+"""Host factor builder checked against the oracle's definition of K (no GPU).
+
+The factors are the product's; what they are compared with is the oracle's dense K, its LU solve
+and the oracle's own product of the packed stages (oracle/factor_apply.py), with the paper's
+error measures e_a = ||K - K-dot|| / ||K|| and e_s = ||I - G-dot K-dot* K|| (section 6)."""
+
+import numpy as np
+import pytest
+
+from oracle import factor_apply as fa
+from oracle import fio_oracle as fo
+from paper_2105_02995_gb300.builder import build_operator
+from paper_2105_02995_gb300.builder.butterfly import build_butterfly, apply_stages
+
+_cache = {}
+
+
+def built(kind, n, eb, eh, **kw):
+    key = (kind, n, eb, eh, tuple(sorted(kw.items())))
+    if key not in _cache:
+        _cache[key] = build_operator(kind, n, eb, eh, **kw)
+    return _cache[key]
+
+
+def spec(A):
+    return np.linalg.norm(A, 2)
+
+
+@pytest.mark.parametrize("kind,n,L,eps", [("ex1", 256, 4, 1e-6), ("ex1", 1024, 6, 1e-9),
+                                          ("ex3", 16, 2, 1e-4), ("ex3", 32, 3, 1e-6)])
+def test_butterfly_error(kind, n, L, eps):
+    """e_a of the butterfly within a small multiple of its tolerance (section 2, eq. for K-dot)."""
+    st, _ = build_butterfly(kind, n, L, eps)
+    op = fo.FIO(kind, n)
+    K = fo.dense_K(op)
+    Kd = apply_stages(st, np.eye(op.N, dtype=complex))
+    assert spec(K - Kd) / spec(K) < 5 * eps
+
+
+@pytest.mark.parametrize("kind,n,eb,eh,bound", [("ex1", 256, 1e-7, 1e-6, 2e-5), ("ex1", 1024, 1e-7, 1e-6, 5e-5),
+                                                ("ex1", 256, 1e-4, 1e-3, 2e-2), ("ex3", 32, 1e-5, 1e-3, 2e-2)])
+def test_inverse_error_es(kind, n, eb, eh, bound):
+    """e_s = ||I - G-dot K-dot* K|| of the packed operator (the paper reports e_s of the order of
+    eps to 10 eps at these sizes, Tables for Examples 1 and 3)."""
+    buf, info = built(kind, n, eb, eh)
+    P = fa.PackedFactors(buf)
+    op = fo.FIO(kind, n)
+    K = fo.dense_K(op)
+    GK = fa.apply_inv(P, K)
+    es = spec(np.eye(op.N) - GK)
+    assert es < bound, es
+
+
+def test_linear_phase_inverse_is_adjoint_over_N():
+    """Phi = x.xi: K*K = N I, so the HIF eliminates every DOF at the leaves (empty root) and
+    G-dot K-dot* = K*/N to the butterfly's accuracy (closed form)."""
+    buf, info = built("linear1d", 256, 1e-10, 1e-8)
+    assert info["root"] == 0
+    P = fa.PackedFactors(buf)
+    op = fo.FIO("linear1d", 256)
+    K = fo.dense_K(op)
+    G = fa.dense_G(P)
+    assert np.max(np.abs(G - np.eye(256) / 256)) < 1e-12
+    assert spec(fa.apply_inv(P, np.eye(256)) - K.conj().T / 256) < 1e-8
+
+
+@pytest.mark.parametrize("kind,n,eb,eh", [("ex1", 256, 1e-7, 1e-6), ("ex3", 32, 1e-5, 1e-3)])
+def test_direct_solve_vs_lu(kind, n, eb, eh):
+    """f = G-dot K-dot* u against the dense LU solve: within 10 eps (spec bound at small N)."""
+    buf, _ = built(kind, n, eb, eh)
+    P = fa.PackedFactors(buf)
+    op = fo.FIO(kind, n)
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal((op.N, 3)) + 1j * rng.standard_normal((op.N, 3))
+    f = fa.apply_inv(P, u)
+    assert fo.rel_err(f, fo.solve_lu(op, u)) < 10 * eh
+
+
+def test_packed_stages_are_bijections():
+    """Every butterfly stage maps onto its output space exactly once in both directions."""
+    import struct
+    buf, _ = built("ex1", 256, 1e-7, 1e-6)
+    nbf = struct.unpack_from("<I", buf, 32)[0]
+    tab = struct.unpack_from("<Q", buf, 64)[0]
+    for s in range(nbf):
+        kind, nblk, R, C = struct.unpack_from("<IIII", buf, tab + 64 * s)
+        il, ol = struct.unpack_from("<qq", buf, tab + 64 * s + 16)
+        oM, oi, oo = struct.unpack_from("<QQQ", buf, tab + 64 * s + 32)
+        ii = np.frombuffer(buf, "<i4", nblk * C, oi)
+        jj = np.frombuffer(buf, "<i4", nblk * R, oo)
+        assert np.array_equal(np.sort(ii[ii >= 0]), np.arange(il))
+        assert np.array_equal(np.sort(jj[jj >= 0]), np.arange(ol))
+
+
+def test_hmatrix_matches_normal_matrix():
+    """Peeling (section 3): S-dot against K-dot* K-dot formed densely, relative error ~ eps."""
+    from paper_2105_02995_gb300.builder.hmatrix import HGeometry, peel
+    st, _ = build_butterfly("ex1", 256, 4, 1e-8)
+    Kd = apply_stages(st, np.eye(256, dtype=complex))
+    A = Kd.conj().T @ Kd
+    H = peel(lambda X: A @ X, HGeometry(1, 256, 3), 1e-6)
+    Sd = H.apply(np.eye(256, dtype=complex))
+    assert spec(A - Sd) / spec(A) < 5e-6

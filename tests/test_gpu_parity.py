@@ -1,0 +1,149 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, element by element.
+
+Two references, both from oracle/:
+  * factor_apply: the same packed factors multiplied out as sparse matrices in FP64.  The FP64
+    GPU path must agree to 1e-12 (relative, Frobenius); the FP32 path to TOL32 below.
+  * fio_oracle: the dense K and its LU solve (the plain definition); the direct solve must be
+    within 10 eps of it at these sizes, iterative solves must reach the residual they report.
+Sizes span several blocks per stage and ragged right-hand-side tiles (b = 1, 3, 5, 16, 37).
+
+TOL32: every stage rounds its outputs to FP32 (unit roundoff 2^-24 ~ 6e-8) after sums of up to
+C_max ~ 300 terms, over up to ~20 stages in a row: 20 * sqrt(300) * 6e-8 ~ 2e-5 relative.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import factor_apply as fa  # noqa: E402
+from oracle import fio_oracle as fo  # noqa: E402
+from paper_2105_02995_gb300 import binding, build as fbuild  # noqa: E402
+from paper_2105_02995_gb300.builder import build_operator  # noqa: E402
+from paper_2105_02995_gb300.inputs import complex_gaussian, rhs_seed  # noqa: E402
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+CASES = {
+    "ex1_256": ("ex1", 256, 1e-7, 1e-6),     # the 1D N = 256, eps = 1e-6 workload
+    "ex1_1024": ("ex1", 1024, 1e-10, 1e-9),
+    "ex3_32": ("ex3", 32, 1e-5, 1e-3),
+}
+_ops = {}
+
+
+def get(name):
+    if name not in _ops:
+        fbuild.build()
+        kind, n, eb, eh = CASES[name]
+        buf, info = build_operator(kind, n, eb, eh)
+        _ops[name] = (buf, info, fa.PackedFactors(buf), binding.Operator(buf), fo.FIO(kind, n))
+    return _ops[name]
+
+
+def dev(a, dtype=torch.complex128):
+    return binding.colmajor(torch.from_numpy(np.asarray(a)).to("cuda", dtype))
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("b", [1, 3, 5, 16, 37])
+def test_apply_fp64_vs_factor_oracle(name, b):
+    buf, info, P, op, ofo = get(name)
+    x = complex_gaussian(ofo.N, b, rhs_seed(0, b))
+    xd = dev(x)
+    for what, ref in (("K", fa.apply_Kdot), ("Kadj", fa.apply_Kdot_adj), ("G", fa.apply_G),
+                      ("inv", fa.apply_inv)):
+        y = getattr(op, "apply_" + what)(xd)
+        torch.cuda.synchronize()
+        assert rel(host(y), ref(P, x)) < TOL64, what
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("b", [1, 8, 32])
+def test_apply_fp32_vs_factor_oracle(name, b):
+    buf, info, P, op, ofo = get(name)
+    x = complex_gaussian(ofo.N, b, rhs_seed(0, 100 + b))
+    xd = dev(x, torch.complex64)
+    for what, ref in (("K", fa.apply_Kdot), ("Kadj", fa.apply_Kdot_adj), ("inv", fa.apply_inv)):
+        y = getattr(op, "apply_" + what)(xd)
+        torch.cuda.synchronize()
+        assert rel(host(y), ref(P, x.astype(np.complex64).astype(np.complex128))) < TOL32, what
+
+
+@pytest.mark.parametrize("name", ["ex1_256", "ex3_32"])
+def test_direct_solve_vs_dense_lu(name):
+    """f = G-dot K-dot* u on the GPU against K^{-1} u by dense LU: within 10 eps."""
+    buf, info, P, op, ofo = get(name)
+    u = complex_gaussian(ofo.N, 4, rhs_seed(0))
+    f = host(op.apply_inv(dev(u)))
+    assert rel(f, fo.solve_lu(ofo, u)) < 10 * CASES[name][3]
+
+
+def test_leading_dimension_and_host_entry():
+    buf, info, P, op, ofo = get("ex1_256")
+    N, b, ld = ofo.N, 5, ofo.N + 7
+    u = complex_gaussian(N, b, rhs_seed(0, 7))
+    big = torch.zeros((b, ld), dtype=torch.complex128, device="cuda")
+    big[:, :N] = torch.from_numpy(u.T.copy()).cuda()
+    ud = big.t()[:N]  # stride (1, ld)
+    assert ud.stride() == (1, ld)
+    fbig = torch.full((b, ld), 7 + 7j, dtype=torch.complex128, device="cuda")
+    fd = fbig.t()[:N]
+    op.apply_inv(ud, fd)
+    torch.cuda.synchronize()
+    want = fa.apply_inv(P, u)
+    assert rel(host(fd), want) < TOL64
+    assert torch.all(fbig[:, N:] == 7 + 7j)  # padding rows untouched
+    fh = op.apply_inv_host(u)
+    assert rel(fh, want) < TOL64
+
+
+def test_invalid_arguments_are_rejected():
+    buf, info, P, op, ofo = get("ex1_256")
+    x = dev(complex_gaussian(ofo.N, 2, 1))
+    with pytest.raises(binding.FioError) as e:
+        op.apply_K(x, x)  # aliasing
+    assert e.value.status == -1
+    lib = binding.load()
+    import ctypes
+    y = torch.empty_like(x)
+    # dtype / precision mismatch
+    assert lib.fio_apply_K(op.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                           ofo.N, 2, 0, 1, None) == -1
+    # ld < N
+    assert lib.fio_apply_K(op.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                           ofo.N - 1, 2, 0, 0, None) == -1
+    # b = 0 is a no-op
+    assert lib.fio_apply_K(op.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                           ofo.N, 0, 0, 0, None) == 0
+
+
+@pytest.mark.parametrize("method", [binding.FIO_PCG, binding.FIO_GMRES, binding.FIO_IR])
+@pytest.mark.parametrize("inner", [binding.FIO_P64, binding.FIO_P32])
+def test_iterative_solves(method, inner):
+    """Solve K-dot f = u to 1e-10; compare with the dense solve of the oracle's K-dot."""
+    name = "ex1_256"
+    buf, info, P, op, ofo = get(name)
+    b = 3
+    u = complex_gaussian(ofo.N, b, rhs_seed(1))
+    f, infos = op.solve(dev(u), method=method, inner=inner, tol=1e-10, maxit=50)
+    torch.cuda.synchronize()
+    Kd = fa.dense_Kdot(P)
+    fh = host(f)
+    for j, (it, rr, st) in enumerate(infos):
+        assert st == 0 and rr <= 1e-10, infos
+        true_rr = np.linalg.norm(u[:, j] - Kd @ fh[:, j]) / np.linalg.norm(u[:, j])
+        assert true_rr < 3e-10
+        assert it <= 12  # the paper: 2-3 PCG iterations at eps = 1e-6
+    f_ex = np.linalg.solve(Kd, u)
+    assert rel(fh, f_ex) < 1e-8
