@@ -1,0 +1,326 @@
+"""Benchmark of the inverse apply f = G-dot K-dot* u (the direct solver of the approximate FIO
+inverse) on the 2D generalized Radon transform, n = 256 (N = 65536), complex64, 32 right-hand
+sides per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+A step is one inverse apply of a batch of b seeded complex-Gaussian right-hand sides already
+resident in HBM.  L2 (129 MB) is flushed by a 256 MB write before every timed step; the flush is
+outside the per-step CUDA-event interval.  value = right-hand sides solved per second by the
+whole job (sum over ranks / max time over ranks).  The factors are built once per operator on the
+host before timing (cached on disk between runs of the same box).
+
+Multi-GPU: replicas only (the right-hand sides are independent): every rank applies its own
+batch with its own copy of the factors; no collective on the data path.
+
+--impl reference times the oracle (oracle/factor_apply.py: the same factors multiplied out as
+sparse matrices in FP64 on the host cores) on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+SMS, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12  # 80.5 TFLOP/s (FFMA = 2 flops)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fio_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def get_operator(a, rank, ws):
+    """Rank 0 builds (or reuses the on-disk cache); the others read the cache after a barrier."""
+    from paper_2105_02995_gb300.builder.__main__ import build_cached
+    if rank == 0:
+        buf, info = build_cached(a.kind, a.n, a.eps_bf, a.eps_hif, gpu=True, verbose=True)
+    barrier(ws)
+    if rank != 0:
+        buf, info = build_cached(a.kind, a.n, a.eps_bf, a.eps_hif, gpu=False, verbose=False)
+    return buf, info
+
+
+def config_of(a, info, l2):
+    return {"workload": f"2D generalized Radon transform (Example 3), n={a.n} (N={a.n * a.n}), direct "
+                        f"inverse apply f = G K* u, complex64, b={a.b} RHS per step",
+            "kind": a.kind, "n": a.n, "N": a.n * a.n, "b": a.b, "eps_bf": a.eps_bf, "eps_hif": a.eps_hif,
+            "L": info.get("L"), "LH": info.get("LH"), "root": info.get("root"), "l2": l2,
+            "parallelism": "replicas"}
+
+
+def cpu_baseline(buf, a, u_np, budget_s=20.0):
+    """The oracle's product of the packed factors (FP64, scipy sparse) on a bounded sample."""
+    from oracle import factor_apply as fa
+    t0 = time.time()
+    P = fa.PackedFactors(buf, verify=False)
+    t_parse = time.time() - t0
+    done, t = 0, 0.0
+    while t < budget_s and done < u_np.shape[1]:
+        s = time.perf_counter()
+        fa.apply_inv(P, u_np[:, done:done + 1])
+        t += time.perf_counter() - s
+        done += 1
+    return {"value": done / t, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of the {a.b} right-hand sides, one at a time, FP64 sparse products "
+                      f"of the same packed factors ({t:.1f} s; factor parse {t_parse:.1f} s untimed)"}
+
+
+def run_reference(a, ws, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_2105_02995_gb300.inputs import complex_gaussian, rhs_seed
+    buf, info = get_operator(a, 0, 1)
+    u = complex_gaussian(a.n * a.n, a.b, rhs_seed(2))
+    from oracle import factor_apply as fa
+    P = fa.PackedFactors(buf, verify=False)
+    for _ in range(a.warmup):
+        fa.apply_inv(P, u[:, :1])
+    times = []
+    for k in range(a.steps):
+        s = time.perf_counter()
+        fa.apply_inv(P, u[:, k % a.b:k % a.b + 1])
+        times.append(time.perf_counter() - s)
+    ms = 1000 * statistics.mean(times)
+    val = 1000.0 / ms
+    line = {"metric": "inverse-apply RHS/s at 2D n=256", "value": val, "unit": "RHS/s", "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": config_of(a, info, "host only"),
+            "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+                             "sample": "one right-hand side per step (of the 32-RHS batch)"},
+            "e2e": {"value": val, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--kind", default="ex3")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--b", type=int, default=32)
+    ap.add_argument("--eps-bf", type=float, default=1e-4)
+    ap.add_argument("--eps-hif", type=float, default=1e-3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    a.warmup = max(3, a.warmup)
+    ws, rank, local = dist_init()
+    if a.impl == "reference":
+        run_reference(a, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2105_02995_gb300 import binding, build as fbuild
+    from paper_2105_02995_gb300.inputs import complex_gaussian, rhs_seed
+    from paper_2105_02995_gb300.packinfo import totals
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        fbuild.build()
+    barrier(ws)
+    buf, info = get_operator(a, rank, ws)
+    op = binding.Operator(buf)
+    N, b = op.N, a.b
+    u_np = complex_gaussian(N, b, rhs_seed(2, rank))
+    u = binding.colmajor(torch.from_numpy(u_np.astype(np.complex64)).cuda())
+    f = binding.colmajor(torch.empty_like(u))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(a.warmup):
+        op.apply_inv(u, f)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(a.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        op.apply_inv(u, f)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier(ws)
+    ck = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    ms = allmax(ws, statistics.mean(step_ms))
+    value = ws * b * 1000.0 / ms
+
+    # per-stage times of the same apply (events after every launch group, same flush discipline)
+    tot = totals(buf)
+    st = tot["stages"]
+    nbf = tot["n_bf"]
+    groups = []  # (label, stage dict or None, direction)
+    for s in reversed(range(nbf)):
+        groups.append(("bf", st[s]))
+    hif = st[nbf:]
+    nh = len(hif) - 1 if hif and hif[-1]["role"] == "root" else len(hif)
+    for s in range(nh):
+        groups.append(("hif", hif[s]))
+    if len(hif) > nh:
+        groups.append(("root", hif[nh]))
+    for s in reversed(range(nh)):
+        groups.append(("hif", hif[s]))
+    groups.append(("layout", None))
+    prof = []
+    for k in range(max(3, min(a.steps, 10))):
+        flush.fill_(float(k))
+        prof.append(op.apply_profiled("inv", u, f))
+    per = [statistics.mean(p[i] for p in prof) for i in range(len(prof[0]))]
+    es = 8  # complex64 bytes
+    kern_time = kern_flops = kern_bytes = 0.0
+    stage_rows = []
+    for (lab, sd), t in zip(groups, per):
+        if sd is None:
+            continue
+        flops = 8.0 * sd["nnz"] * b
+        byt = es * sd["nnz"] + es * b * (sd["in_len"] + sd["out_len"] if lab == "bf" else 2 * sd["touched"])
+        kern_time += t
+        kern_flops += flops
+        kern_bytes += byt
+        stage_rows.append({"group": lab, "role": sd["role"], "level": sd["level"], "ms": round(t, 4),
+                           "tflops": round(flops / t / 1e9, 2), "gbs": round(byt / t / 1e6, 1)})
+    peaks, src = measured_peaks()
+    achieved = kern_flops / (kern_time / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
+            "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+            "kernel": "k_stage_mm (every stage launch of one apply, float2, b=32)",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+            "hbm_view": {"achieved_gbs": round(kern_bytes / (kern_time / 1e3) / 1e9, 1),
+                         "peak_gbs": peaks.get("hbm_gbs"), "peak_source": src},
+            "stage_ms_sum": round(kern_time, 4), "step_ms": round(ms, 4)}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    uh = torch.from_numpy(u_np.astype(np.complex64)).t().contiguous().pin_memory()  # (b, N) rows = RHS
+    fh = torch.empty_like(uh).pin_memory()
+    uh_np, fh_np = uh.numpy().T, fh.numpy().T  # (N, b) Fortran views
+    for _ in range(2):
+        op.apply_inv_host(uh_np, fh_np)
+    barrier(ws)
+    s = time.perf_counter()
+    for _ in range(a.steps):
+        op.apply_inv_host(uh_np, fh_np)
+    e2e_ms = allmax(ws, 1000 * (time.perf_counter() - s) / a.steps)
+    e2e = {"value": ws * b * 1000.0 / e2e_ms, "unit": "RHS/s", "h2d_bytes_per_step": N * b * 8,
+           "d2h_bytes_per_step": N * b * 8, "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(buf, a, u_np)
+    launches = op.launches("inv", b) * a.steps
+    if rank == 0:
+        line = {"metric": "inverse-apply RHS/s at 2D n=256", "value": round(value, 2), "unit": "RHS/s",
+                "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": config_of(a, info, "flushed before every step (256 MB write)"),
+                "rhs_N_per_s": round(value * N, 1), "wall_ms_per_step": round(1000 * t_wall / a.steps, 4),
+                "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+                "cpu_baseline": cpu, "stages": stage_rows,
+                "factors": {"P_K": tot["P_K"], "P_G": tot["P_G"], "padded_K": tot["padded_K"],
+                            "padded_G": tot["padded_G"], "bytes_c64": 8 * (tot["padded_K"] + tot["padded_G"]),
+                            "build_s": {k: info.get(k) for k in ("t_bf", "t_peel", "t_hif", "t_total")}}}
+        print(json.dumps(line), flush=True)
+    op.release()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,6 +146,13 @@ int fio_query(fio_op op, int* d, int64_t* n, int64_t* N, size_t* device_bytes);
  * which = 0 apply_K, 1 apply_Kadj, 2 apply_G, 3 apply_inv. */
 int fio_launch_count(fio_op op, int which, int b, int* launches);
 
+/* Diagnostics: the apply `which` (as in fio_launch_count) with a CUDA event recorded on `stream`
+ * after every launch group (one butterfly stage; one HIF stage = its compute and copy-back
+ * launches; a layout change).  stage_ms[k] (host, cap entries) receives the time of group k in
+ * launch order, *nmarks the number of groups.  Synchronises `stream`.  Not for the timed path. */
+int fio_apply_profiled(fio_op op, int which, const void* x, void* y, int64_t ld, int b, int dtype,
+                       int precision, void* stream, float* stage_ms, int cap, int* nmarks);
+
 /* Free the device copies and scratch of op (synchronises the device first).  NULL is a no-op. */
 int fio_release(fio_op op);
 

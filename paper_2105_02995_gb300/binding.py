@@ -25,8 +25,8 @@ FIO_MASK_P64, FIO_MASK_P32 = 1, 2
 STATUS = {0: "FIO_OK", -1: "FIO_EINVAL", -2: "FIO_ENOMEM", -3: "FIO_EBADFACTORS",
           -4: "FIO_ENOCONV", -5: "FIO_ETIMEOUT", -6: "FIO_ECUDA", -7: "FIO_ENOTSUP"}
 SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv",
-           "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_release",
-           "fio_strerror"]
+           "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_apply_profiled",
+           "fio_release", "fio_strerror"]
 
 _lib = None
 
@@ -63,6 +63,8 @@ def load(path: str = LIB_PATH):
     lib.fio_query.argtypes = [vp, ctypes.POINTER(c_int), ctypes.POINTER(i64), ctypes.POINTER(i64),
                               ctypes.POINTER(ctypes.c_size_t)]
     lib.fio_launch_count.argtypes = [vp, c_int, c_int, ctypes.POINTER(c_int)]
+    lib.fio_apply_profiled.argtypes = [vp, c_int, vp, vp, i64, c_int, c_int, c_int, vp,
+                                       ctypes.POINTER(ctypes.c_float), c_int, ctypes.POINTER(c_int)]
     lib.fio_release.argtypes = [vp]
     lib.fio_strerror.argtypes = [c_int]
     lib.fio_strerror.restype = ctypes.c_char_p
@@ -148,6 +150,18 @@ class Operator:
                   prec, _stream()), name)
         return y
 
+    def apply_profiled(self, which: str, x, y):
+        """Per-launch-group times (ms) of one apply, in launch order (fio_apply_profiled)."""
+        k = {"K": 0, "Kadj": 1, "G": 2, "inv": 3}[which]
+        dt, prec, b, ld = _vec(x, self.N)
+        cap = 4096
+        ms = (ctypes.c_float * cap)()
+        nm = ctypes.c_int()
+        _check(self._lib.fio_apply_profiled(self.h, k, ctypes.c_void_p(x.data_ptr()),
+                                            ctypes.c_void_p(y.data_ptr()), ld, b, dt, prec, _stream(),
+                                            ms, cap, ctypes.byref(nm)), "fio_apply_profiled")
+        return [ms[i] for i in range(nm.value)]
+
     def apply_K(self, x, y=None):
         return self._apply(self._lib.fio_apply_K, "fio_apply_K", x, y)
 
@@ -217,15 +231,8 @@ class NormalMatvecGPU:
         self.precision = precision
         self.chunk = chunk
 
-    def bind(self, bf_stages):
+    def bind(self, bf_stages, d: int, n: int):
         from .builder.pack import pack
-        st0 = bf_stages[0]
-        N = st0.in_len
-        d = 1
-        n = N
-        r = int(round(N ** 0.5))
-        if getattr(self, "d", None) == 2 or (hasattr(self, "grid") and self.grid == 2):
-            d, n = 2, r
         packed = pack(d, n, bf_stages, [], [], 0.0, 0.0)
         op = Operator(packed)
         prec = self.precision

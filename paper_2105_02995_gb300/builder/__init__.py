@@ -80,16 +80,23 @@ def build_operator(kind: str, n: int, eps_bf: float, eps_hif: float, L: int = No
     t0 = time.time()
     bf, bfinfo = build_butterfly(kind, n, L, eps_bf, seed=seed)
     t1 = time.time()
+    if verbose:
+        print(f"[build] butterfly {kind} n={n} L={L}: {t1 - t0:.1f} s, max middle rank "
+              f"{bfinfo['mid_rank_max']}, {bfinfo['nnz'] / n ** d:.0f} entries per DOF", flush=True)
     if mv is None:
         ps = PaddedStages(bf)
         mv = lambda X: ps.apply(ps.apply(X), adjoint=True)  # noqa: E731
     elif callable(getattr(mv, "bind", None)):
-        mv = mv.bind(bf)
+        mv = mv.bind(bf, d, n)
     geom = HGeometry(d, n, LH)
     H = peel(mv, geom, eps_hif, seed=seed + 1)
     t2 = time.time()
+    if verbose:
+        print(f"[build] peeling L_H={LH}: {t2 - t1:.1f} s, ranks {H.ranks()}", flush=True)
     hif_stages, hif = build_hif(H, eps_hif)
     t3 = time.time()
+    if verbose:
+        print(f"[build] HIF: {t3 - t2:.1f} s, root {hif.root_size}, steps {hif.stats}", flush=True)
     buf = pack(d, n, bf, hif_stages[:-1], hif_stages[-1:], eps_bf, eps_hif, flags=(d == 2))
     info = dict(kind=kind, n=n, d=d, N=n ** d, L=L, LH=LH, eps_bf=eps_bf, eps_hif=eps_hif,
                 t_bf=t1 - t0, t_peel=t2 - t1, t_hif=t3 - t2, root=hif.root_size,

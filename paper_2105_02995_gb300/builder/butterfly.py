@@ -23,10 +23,14 @@ Each factor becomes one MAP stage (stages.py), L + 3 in all:
 
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import scipy.linalg as sla
 
 from .entries import FIOEntries
+from . import blas
 from .geometry import Tree
 from .stages import KIND_MAP, ROLE_BF, Stage
 
@@ -70,6 +74,10 @@ def lowrank_block(ent: FIOEntries, P: np.ndarray, Q: np.ndarray, eps: float,
         s *= 2
 
 
+def _workers() -> int:
+    return blas.pool_workers()
+
+
 def _descend(blocks: dict, s0: int, L: int, beta: int, tree: Tree, eps: float):
     """Nested-basis recursion on one side (section 2, eq. U_l = U_{l+1} C_l).
 
@@ -78,20 +86,28 @@ def _descend(blocks: dict, s0: int, L: int, beta: int, tree: Tree, eps: float):
     r' x (sum_k r_{a, b_k}) matrix, leaves[(leaf, 0)] the final leaf bases.
     """
     transfers = []
-    for s in range(s0, L):
-        nxt, T = {}, {}
-        rows = tree.size(s + 1)
-        for a in range(beta ** s):
-            for bp in range(beta ** (L - s - 1)):
-                bks = [beta * bp + k for k in range(beta)]
-                for c in range(beta):
-                    cat = np.hstack([blocks[(a, bk)][c * rows:(c + 1) * rows] for bk in bks])
-                    Uq, sv, Wh = np.linalg.svd(cat, full_matrices=False)
-                    r = _rank(sv, eps)
-                    nxt[(beta * a + c, bp)] = Uq[:, :r]
-                    T[(beta * a + c, bp)] = sv[:r, None] * Wh[:r]
-        transfers.append(T)
-        blocks = nxt
+    with blas.threads(1), ThreadPoolExecutor(_workers()) as ex:
+        for s in range(s0, L):
+            rows = tree.size(s + 1)
+
+            def one(a, s=s, rows=rows, blocks=blocks):
+                res = []
+                for bp in range(beta ** (L - s - 1)):
+                    bks = [beta * bp + k for k in range(beta)]
+                    for c in range(beta):
+                        cat = np.hstack([blocks[(a, bk)][c * rows:(c + 1) * rows] for bk in bks])
+                        Uq, sv, Wh = np.linalg.svd(cat, full_matrices=False)
+                        r = _rank(sv, eps)
+                        res.append(((beta * a + c, bp), Uq[:, :r], sv[:r, None] * Wh[:r]))
+                return res
+
+            nxt, T = {}, {}
+            for res in ex.map(one, range(beta ** s)):
+                for key, U, C in res:
+                    nxt[key] = U
+                    T[key] = C
+            transfers.append(T)
+            blocks = nxt
     return transfers, blocks
 
 
@@ -115,17 +131,26 @@ def build_butterfly(kind: str, n: int, L: int, eps: float, seed: int = 20210506)
     tree = Tree(d, n, L)
     beta = tree.beta
     h = L // 2  # X middle level; the Omega middle level is L - h
-    rng = np.random.Generator(np.random.PCG64(seed))
+    # sample size of the first try: the rank of one probe block plus oversampling
+    P0, Q0 = tree.points(h, 0), tree.points(L - h, 0)
+    U0, _, _ = lowrank_block(ent, P0, Q0, eps, np.random.Generator(np.random.PCG64([seed, 0, 0])))
+    s_first = U0.shape[1] + 24
+
+    def one(i):
+        P = tree.points(h, i)
+        res = []
+        for j in range(beta ** (L - h)):
+            rng = np.random.Generator(np.random.PCG64([seed, i, j]))
+            res.append((j, lowrank_block(ent, P, tree.points(L - h, j), eps, rng, s0=s_first)))
+        return i, res
 
     Ublk, Vblk, Dblk = {}, {}, {}
-    for i in range(beta ** h):
-        P = tree.points(h, i)
-        for j in range(beta ** (L - h)):
-            Q = tree.points(L - h, j)
-            U, D, V = lowrank_block(ent, P, Q, eps, rng)
-            Ublk[(i, j)] = U
-            Vblk[(j, i)] = V
-            Dblk[(i, j)] = D
+    with blas.threads(1), ThreadPoolExecutor(_workers()) as ex:
+        for i, res in ex.map(one, range(beta ** h)):
+            for j, (U, D, V) in res:
+                Ublk[(i, j)] = U
+                Vblk[(j, i)] = V
+                Dblk[(i, j)] = D
 
     Ctr, Uleaf = _descend(Ublk, h, L, beta, tree, eps)
     Htr, Vleaf = _descend(Vblk, L - h, L, beta, tree, eps)

@@ -25,9 +25,13 @@ and the 2D product with Rbar_l between the cell factors (eq. for G-dot in 2D).
 
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import scipy.linalg as sla
 
+from . import blas
 from .hmatrix import HMatrix
 from .stages import KIND_INPLACE, ROLE_HIF_CELL, ROLE_HIF_EDGE, ROLE_ROOT, Stage
 
@@ -148,22 +152,38 @@ class HIF:
                 self.near[(c, c2)] = self.near[(c, c2)][keep_pos]
                 self.near[(c2, c)] = self.near[(c2, c)][:, keep_pos]
 
+    def _pool(self):
+        return ThreadPoolExecutor(blas.pool_workers())
+
     def _cells(self, lvl: int):
+        """Cell skeletonization of every cell of `lvl`.  The cells' index sets are disjoint and each
+        elimination changes only its own diagonal block, so all IDs and eliminations are computed
+        from the level's starting state (in parallel) and the updates applied afterwards."""
         g = self.g
         st = Stage(KIND_INPLACE, self.t.N, self.t.N, ROLE_HIF_CELL, level=lvl)
-        nred = 0
-        for c in range(g.beta ** lvl):
+
+        def work(c):
             I = self.dofs[c]
-            if len(I) == 0:
-                continue
             rows = [self.near[(c2, c)] for c2 in g.NL[lvl][c] if c2 != c]
             rows += self._far_rows(lvl, c, I)
             Ub = np.vstack(rows) if rows else np.zeros((0, len(I)))
             skel, red, T = interp_decomp(Ub, self.eps, len(I))
             if len(red) == 0:
-                continue
+                return c, None
             M, schur = eliminate(self.near[(c, c)], red, skel, T)
-            st.add(M, np.concatenate([I[red], I[skel]]), np.concatenate([I[red], I[skel]]))
+            return c, (red, skel, M, schur)
+
+        cells = [c for c in range(g.beta ** lvl) if len(self.dofs[c])]
+        with blas.threads(1), self._pool() as ex:
+            results = list(ex.map(work, cells))
+        nred = 0
+        for c, res in results:
+            if res is None:
+                continue
+            red, skel, M, schur = res
+            I = self.dofs[c]
+            order = np.concatenate([I[red], I[skel]])
+            st.add(M, order, order)
             nred += len(red)
             self.near[(c, c)][np.ix_(skel, skel)] = schur
             self._restrict(c, np.sort(skel), lvl)
@@ -201,28 +221,29 @@ class HIF:
                 groups.setdefault(key, {})[c] = I[sel]
         return groups
 
-    def _edges(self, lvl: int):
-        g, t = self.g, self.t
+    def _edge_cells(self, lvl, key):
+        t = self.t
         m = 2 ** lvl
+        kind, e1, e2 = key
+        if kind == "v":
+            return int(t.cell_id(lvl, (e1 - 1) % m, e2)), int(t.cell_id(lvl, e1, e2))
+        return int(t.cell_id(lvl, e1, (e2 - 1) % m)), int(t.cell_id(lvl, e1, e2))
+
+    def _edges(self, lvl: int):
+        """Edge skeletonization (2D): like _cells, every edge is computed from the level's state
+        after the cell step, then the Schur complements and removals are applied in order."""
+        g, t = self.g, self.t
         st = Stage(KIND_INPLACE, t.N, t.N, ROLE_HIF_EDGE, level=lvl)
-        nred = 0
         groups = self._edge_assign(lvl)
-        for key in sorted(groups):
-            kind, e1, e2 = key
-            if kind == "v":
-                c1 = int(t.cell_id(lvl, (e1 - 1) % m, e2))
-                c2 = int(t.cell_id(lvl, e1, e2))
-            else:
-                c1 = int(t.cell_id(lvl, e1, (e2 - 1) % m))
-                c2 = int(t.cell_id(lvl, e1, e2))
-            # current positions of the edge's DOFs (earlier edges may have shrunk the cells)
+
+        def work(key):
+            c1, c2 = self._edge_cells(lvl, key)
             p1 = self._pos_of(c1, groups[key].get(c1))
             p2 = self._pos_of(c2, groups[key].get(c2))
             I1, I2 = self.dofs[c1][p1], self.dofs[c2][p2]
             nI1, nI = len(I1), len(I1) + len(I2)
             if nI == 0:
-                continue
-            # near-field rows
+                return None
             cells = np.union1d(g.NL[lvl][c1], g.NL[lvl][c2])
             rows = []
             for cc in cells:
@@ -252,7 +273,7 @@ class HIF:
             Ub = np.vstack(rows) if rows else np.zeros((0, nI))
             skel, red, T = interp_decomp(Ub, self.eps, nI)
             if len(red) == 0:
-                continue
+                return None
             A = np.empty((nI, nI), dtype=np.complex128)
             A[:nI1, :nI1] = self.near[(c1, c1)][np.ix_(p1, p1)]
             A[nI1:, nI1:] = self.near[(c2, c2)][np.ix_(p2, p2)]
@@ -260,27 +281,33 @@ class HIF:
             A[nI1:, :nI1] = self.near[(c2, c1)][np.ix_(p2, p1)]
             M, schur = eliminate(A, red, skel, T)
             I = np.concatenate([I1, I2])
-            st.add(M, np.concatenate([I[red], I[skel]]), np.concatenate([I[red], I[skel]]))
+            return (c1, c2, I, nI1, red, skel, M, schur)
+
+        keys = sorted(groups)
+        with blas.threads(1), self._pool() as ex:
+            results = list(ex.map(work, keys))
+        nred = 0
+        for res in results:
+            if res is None:
+                continue
+            c1, c2, I, nI1, red, skel, M, schur = res
+            order = np.concatenate([I[red], I[skel]])
+            st.add(M, order, order)
             nred += len(red)
-            # write the Schur complement back into the near blocks
-            sk1 = skel[skel < nI1]
-            sk2 = skel[skel >= nI1] - nI1
             o1 = skel < nI1
             o2 = ~o1
-            S11 = schur[np.ix_(o1, o1)]
-            S22 = schur[np.ix_(o2, o2)]
+            q1 = self._pos_of(c1, I[skel[o1]])
+            q2 = self._pos_of(c2, I[skel[o2]])
+            self.near[(c1, c1)][np.ix_(q1, q1)] = schur[np.ix_(o1, o1)]
+            self.near[(c2, c2)][np.ix_(q2, q2)] = schur[np.ix_(o2, o2)]
             S12 = schur[np.ix_(o1, o2)]
-            self.near[(c1, c1)][np.ix_(p1[sk1], p1[sk1])] = S11
-            self.near[(c2, c2)][np.ix_(p2[sk2], p2[sk2])] = S22
-            self.near[(c1, c2)][np.ix_(p1[sk1], p2[sk2])] = S12
-            self.near[(c2, c1)][np.ix_(p2[sk2], p1[sk1])] = S12.conj().T
-            # remove the redundant DOFs
-            red1 = p1[red[red < nI1]]
-            red2 = p2[red[red >= nI1] - nI1]
-            keep1 = np.setdiff1d(np.arange(len(self.dofs[c1])), red1)
-            self._restrict(c1, keep1, lvl)
-            keep2 = np.setdiff1d(np.arange(len(self.dofs[c2])), red2)
-            self._restrict(c2, keep2, lvl)
+            self.near[(c1, c2)][np.ix_(q1, q2)] = S12
+            self.near[(c2, c1)][np.ix_(q2, q1)] = S12.conj().T
+            rr = I[red]
+            for c in (c1, c2):
+                drop = np.isin(self.dofs[c], rr)
+                if drop.any():
+                    self._restrict(c, np.nonzero(~drop)[0], lvl)
         if st.blocks:
             self.stages.append(st)
         self.stats.append(("edge", lvl, nred, sum(len(v) for v in self.dofs.values())))

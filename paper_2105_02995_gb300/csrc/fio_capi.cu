@@ -250,6 +250,19 @@ int fio_scratch(fio_op op, int b, size_t elem, cudaStream_t s, void** bufs) {
 // ---------------------------------------------------------------------------------------------
 namespace {
 
+// optional per-stage event marks (fio_apply_profiled); null in the ordinary applies
+struct Marks {
+  cudaEvent_t* ev;
+  int cap, n;
+  void mark(cudaStream_t s) {
+    if (ev && n < cap) cudaEventRecord(ev[n++], s);
+  }
+};
+thread_local Marks* g_marks = nullptr;
+inline void mark(cudaStream_t s) {
+  if (g_marks) g_marks->mark(s);
+}
+
 template <typename V> const V* stage_M(const Stage& st);
 template <> const double2* stage_M<double2>(const Stage& st) { return st.M64; }
 template <> const float2* stage_M<float2>(const Stage& st) { return st.M32; }
@@ -318,6 +331,7 @@ void inplace_stage(const Stage& st, bool adj, V* W, V* S, int b, cudaStream_t s)
   const long long nidx = (long long)st.nblk * st.R;
   const long long tot = nidx * b;
   k_scatter_back<V><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(st.out, nidx, S, W, b);
+  mark(s);
 }
 
 // K-dot (adj = false) or K-dot* (adj = true): x (xrs, xcs) -> y (yrs, ycs); A, B ping-pong
@@ -333,6 +347,7 @@ void bf_chain(fio_op op, bool adj, const V* x, long long xrs, long long xcs, V* 
     V* dst = last ? y : ((k & 1) ? B : A);
     const long long drs = last ? yrs : b, dcs = last ? ycs : 1;
     launch_stage<V>(st, adj, cur, crs, ccs, dst, drs, dcs, b, s);
+    mark(s);
     cur = dst;
     crs = drs;
     ccs = dcs;
@@ -352,11 +367,13 @@ template <typename V>
 void to_row(const V* X, long long ld, V* W, long long N, int b, cudaStream_t s) {
   dim3 grid((unsigned)((N + 31) / 32), (unsigned)((b + 31) / 32));
   k_col_to_row<V><<<grid, dim3(32, 8), 0, s>>>(X, ld, W, N, b);
+  mark(s);
 }
 template <typename V>
 void to_col(const V* W, V* Y, long long ld, long long N, int b, cudaStream_t s) {
   dim3 grid((unsigned)((N + 31) / 32), (unsigned)((b + 31) / 32));
   k_row_to_col<V><<<grid, dim3(32, 8), 0, s>>>(W, Y, ld, N, b);
+  mark(s);
 }
 
 int check_args(fio_op op, const void* x, const void* y, int64_t ld, int b, int dtype, int prec) {
@@ -476,4 +493,35 @@ extern "C" int fio_launch_count(fio_op op, int which, int b, int* launches) {
     case 3: *launches = b ? bfl + gl + 1 : 0; break;
   }
   return FIO_OK;
+}
+
+extern "C" int fio_apply_profiled(fio_op op, int which, const void* x, void* y, int64_t ld, int b,
+                                  int dtype, int precision, void* stream, float* stage_ms, int cap,
+                                  int* nmarks) {
+  if (!stage_ms || cap <= 0 || !nmarks || which < 0 || which > 3) return FIO_EINVAL;
+  int rc = check_args(op, x, y, ld, b, dtype, precision);
+  if (rc) return rc;
+  if ((which == 2 || which == 3) && op->n_root == 0) return FIO_ENOTSUP;
+  if (b == 0) {
+    *nmarks = 0;
+    return FIO_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<cudaEvent_t> ev((size_t)cap + 1);
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return FIO_ECUDA;
+  Marks m{ev.data() + 1, cap, 0};
+  cudaEventRecord(ev[0], s);
+  g_marks = &m;
+  rc = precision == FIO_P64 ? apply_t<double2>(op, (Which)which, x, y, ld, b, s)
+                            : apply_t<float2>(op, (Which)which, x, y, ld, b, s);
+  g_marks = nullptr;
+  if (rc == FIO_OK) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = FIO_ECUDA;
+    for (int k = 0; rc == FIO_OK && k < m.n; ++k)
+      if (cudaEventElapsedTime(&stage_ms[k], ev[k], ev[k + 1]) != cudaSuccess) rc = FIO_ECUDA;
+    *nmarks = m.n;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return rc;
 }
