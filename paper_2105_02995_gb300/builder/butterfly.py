@@ -19,6 +19,12 @@ structure of the K-dot equation serves, and the result is checked against the de
 Each factor becomes one MAP stage (stages.py), L + 3 in all:
   V_L* (leaf points -> coefficients), H*_{L-1} .. H*_{L-h}, D, C_h .. C_{L-1}, U_L (coefficients
   -> leaf points).  Coefficient vectors list the pairs in node-major order with their true ranks.
+
+Weighted variant (the default): the middle singular values are split between both sides
+(U sqrt(D), V sqrt(D)) and every nested-basis SVD hands its singular values down with the basis,
+so each truncation is relative to what the directions contribute to K rather than to an
+orthonormal basis; D is then the identity, a pure permutation of coefficient slots, and is folded
+into the index lists of the last H* stage (L + 2 stages).
 """
 
 from __future__ import annotations
@@ -78,7 +84,7 @@ def _workers() -> int:
     return blas.pool_workers()
 
 
-def _descend(blocks: dict, s0: int, L: int, beta: int, tree: Tree, eps: float):
+def _descend(blocks: dict, s0: int, L: int, beta: int, tree: Tree, eps: float, weighted: bool = False):
     """Nested-basis recursion on one side (section 2, eq. U_l = U_{l+1} C_l).
 
     blocks[(a, b)]: basis (n_a x r) of own-tree node a at level s0 paired with other-tree node b at
@@ -98,7 +104,12 @@ def _descend(blocks: dict, s0: int, L: int, beta: int, tree: Tree, eps: float):
                         cat = np.hstack([blocks[(a, bk)][c * rows:(c + 1) * rows] for bk in bks])
                         Uq, sv, Wh = np.linalg.svd(cat, full_matrices=False)
                         r = _rank(sv, eps)
-                        res.append(((beta * a + c, bp), Uq[:, :r], sv[:r, None] * Wh[:r]))
+                        if weighted:
+                            # keep the singular values with the basis handed to the next level, so
+                            # every truncation is relative to what the directions contribute
+                            res.append(((beta * a + c, bp), Uq[:, :r] * sv[:r], Wh[:r]))
+                        else:
+                            res.append(((beta * a + c, bp), Uq[:, :r], sv[:r, None] * Wh[:r]))
                 return res
 
             nxt, T = {}, {}
@@ -121,7 +132,7 @@ def _offsets(ranks: dict, n_a: int, n_b: int):
     return off, cur
 
 
-def build_butterfly(kind: str, n: int, L: int, eps: float, seed: int = 20210506):
+def build_butterfly(kind: str, n: int, L: int, eps: float, seed: int = 20210506, weighted: bool = True):
     """Factor K for the operator (kind, n) with a depth-L tree at tolerance eps.
 
     Returns (stages, info): stages in application order for K-dot x (first applied first).
@@ -131,10 +142,13 @@ def build_butterfly(kind: str, n: int, L: int, eps: float, seed: int = 20210506)
     tree = Tree(d, n, L)
     beta = tree.beta
     h = L // 2  # X middle level; the Omega middle level is L - h
-    # sample size of the first try: the rank of one probe block plus oversampling
-    P0, Q0 = tree.points(h, 0), tree.points(L - h, 0)
-    U0, _, _ = lowrank_block(ent, P0, Q0, eps, np.random.Generator(np.random.PCG64([seed, 0, 0])))
-    s_first = U0.shape[1] + 24
+    # sample size of the first try: the largest rank of a few probe blocks plus oversampling
+    nX, nO = beta ** h, beta ** (L - h)
+    probe = [(0, 0), (nX // 2, nO // 2), (nX - 1, nO // 3), (nX // 3, nO - 1)]
+    r0 = max(lowrank_block(ent, tree.points(h, i), tree.points(L - h, j), eps,
+                           np.random.Generator(np.random.PCG64([seed, i, j])))[0].shape[1]
+             for i, j in probe)
+    s_first = int(1.2 * r0) + 24
 
     def one(i):
         P = tree.points(h, i)
@@ -152,8 +166,15 @@ def build_butterfly(kind: str, n: int, L: int, eps: float, seed: int = 20210506)
                 Vblk[(j, i)] = V
                 Dblk[(i, j)] = D
 
-    Ctr, Uleaf = _descend(Ublk, h, L, beta, tree, eps)
-    Htr, Vleaf = _descend(Vblk, L - h, L, beta, tree, eps)
+    if weighted:
+        # K_ij = (U sqrt D)(V sqrt D)^*: both sides carry the weights, the middle factor is I
+        for key in Ublk:
+            w = np.sqrt(Dblk[key])
+            Ublk[key] = Ublk[key] * w
+            Vblk[(key[1], key[0])] = Vblk[(key[1], key[0])] * w
+            Dblk[key] = np.ones_like(w)
+    Ctr, Uleaf = _descend(Ublk, h, L, beta, tree, eps, weighted)
+    Htr, Vleaf = _descend(Vblk, L - h, L, beta, tree, eps, weighted)
 
     # ranks per level on each side: Ur[s][(i, j)] at X-level s; Vr[t][(j, i)] at Omega-level t
     Ur = {h: {k: v.shape[1] for k, v in Ublk.items()}}
@@ -183,24 +204,31 @@ def build_butterfly(kind: str, n: int, L: int, eps: float, seed: int = 20210506)
         V = Vleaf[(j, 0)]
         st.add(V.conj().T, tree.points(L, j), vslots(L, j, 0))
     stages.append(st)
-    # 2. H*_t for t = L-1 .. L-h: Omega-level t+1 coefficients -> Omega-level t
+    # 2. H*_t for t = L-1 .. L-h: Omega-level t+1 coefficients -> Omega-level t.  With weighted
+    #    bases the middle factor D is the identity, a permutation of the coefficient slots; it is
+    #    folded into the output indices of the last H* stage (which then writes the U slots).
     for t in range(L - 1, L - h - 1, -1):
         Hd = Htr[t - (L - h)]
-        st = Stage(KIND_MAP, Voff[t + 1][1], Voff[t][1], ROLE_BF, level=t)
+        fold = weighted and t == L - h
+        st = Stage(KIND_MAP, Voff[t + 1][1], Uoff[h][1] if fold else Voff[t][1], ROLE_BF, level=t)
         for j in range(beta ** t):
             for ih in range(beta ** (L - t - 1)):
                 kids = [beta * j + k for k in range(beta)]
                 M = np.hstack([Hd[(jk, ih)].conj().T for jk in kids])
                 inp = np.concatenate([vslots(t + 1, jk, ih) for jk in kids])
-                out = np.concatenate([vslots(t, j, beta * ih + c) for c in range(beta)])
+                if fold:
+                    out = np.concatenate([uslots(h, beta * ih + c, j) for c in range(beta)])
+                else:
+                    out = np.concatenate([vslots(t, j, beta * ih + c) for c in range(beta)])
                 st.add(M, inp, out)
         stages.append(st)
     # 3. D: (j, i) at Omega-level L-h -> (i, j) at X-level h
-    st = Stage(KIND_MAP, Voff[L - h][1], Uoff[h][1], ROLE_BF, level=h)
-    for i in range(beta ** h):
-        for j in range(beta ** (L - h)):
-            st.add(np.diag(Dblk[(i, j)]), vslots(L - h, j, i), uslots(h, i, j))
-    stages.append(st)
+    if not weighted:
+        st = Stage(KIND_MAP, Voff[L - h][1], Uoff[h][1], ROLE_BF, level=h)
+        for i in range(beta ** h):
+            for j in range(beta ** (L - h)):
+                st.add(np.diag(Dblk[(i, j)]), vslots(L - h, j, i), uslots(h, i, j))
+        stages.append(st)
     # 4. C_s for s = h .. L-1: X-level s coefficients -> X-level s+1
     for s in range(h, L):
         Cd = Ctr[s - h]

@@ -36,16 +36,22 @@ from .hmatrix import HMatrix
 from .stages import KIND_INPLACE, ROLE_HIF_CELL, ROLE_HIF_EDGE, ROLE_ROOT, Stage
 
 
-def interp_decomp(Ub: np.ndarray, eps: float, ncols: int):
-    """ID by column-pivoted QR: returns (skel positions, redundant positions, T)."""
+def interp_decomp(Ub: np.ndarray, eps: float, ncols: int, abs_tol: float = 0.0):
+    """ID by column-pivoted QR: returns (skel positions, redundant positions, T).
+
+    Columns are redundant once the pivoted QR's diagonal falls below max(eps |R_11|, abs_tol)."""
     if Ub.shape[0] == 0 or ncols == 0:
         return np.zeros(0, dtype=np.int64), np.arange(ncols), np.zeros((0, ncols))
     nrm = np.linalg.norm(Ub)
     if nrm == 0:
         return np.zeros(0, dtype=np.int64), np.arange(ncols), np.zeros((0, ncols))
-    Q, R, P = sla.qr(Ub, mode="economic", pivoting=True)
+    if Ub.shape[0] > ncols:
+        # U-bar = Q R with Q orthonormal: the column ID of R is the column ID of U-bar, and the
+        # unpivoted (blocked) QR of a tall matrix is much cheaper than the pivoted one
+        Ub = sla.qr(Ub, mode="r", overwrite_a=False, check_finite=False)[0][:ncols]
+    Q, R, P = sla.qr(Ub, mode="economic", pivoting=True, check_finite=False)
     diag = np.abs(np.diag(R))
-    k = int(np.count_nonzero(diag > eps * diag[0])) if diag.size else 0
+    k = int(np.count_nonzero(diag > max(eps * diag[0], abs_tol))) if diag.size else 0
     if k == 0:
         return np.zeros(0, dtype=np.int64), np.arange(ncols), np.zeros((0, ncols))
     T = sla.solve_triangular(R[:k, :k], R[:k, k:], lower=False)
@@ -80,7 +86,8 @@ def eliminate(A: np.ndarray, red: np.ndarray, skel: np.ndarray, T: np.ndarray):
 
 
 class HIF:
-    def __init__(self, H: HMatrix, eps: float, edges: bool = None, stop_level: int = None):
+    def __init__(self, H: HMatrix, eps: float, edges: bool = None, stop_level: int = None,
+                 tol_mode: str = "local"):
         self.H = H
         self.g = H.geom
         self.t = self.g.tree
@@ -90,6 +97,9 @@ class HIF:
         if stop_level is None:
             stop_level = 1 if d == 1 else 2
         self.stop = min(stop_level, self.g.LH)
+        # "local": relative to each node's U-bar (the paper's ID accuracy statement);
+        # "global": also accept columns whose residual is below eps ||A||_2
+        self.abs_tol = eps * H.normA if tol_mode == "global" else 0.0
         self.stages = []
         self.stats = []
         self._far_factors()
@@ -167,7 +177,7 @@ class HIF:
             rows = [self.near[(c2, c)] for c2 in g.NL[lvl][c] if c2 != c]
             rows += self._far_rows(lvl, c, I)
             Ub = np.vstack(rows) if rows else np.zeros((0, len(I)))
-            skel, red, T = interp_decomp(Ub, self.eps, len(I))
+            skel, red, T = interp_decomp(Ub, self.eps, len(I), self.abs_tol)
             if len(red) == 0:
                 return c, None
             M, schur = eliminate(self.near[(c, c)], red, skel, T)
@@ -271,7 +281,7 @@ class HIF:
                         blk[:, nI1:] = F
                     rows.append(blk)
             Ub = np.vstack(rows) if rows else np.zeros((0, nI))
-            skel, red, T = interp_decomp(Ub, self.eps, nI)
+            skel, red, T = interp_decomp(Ub, self.eps, nI, self.abs_tol)
             if len(red) == 0:
                 return None
             A = np.empty((nI, nI), dtype=np.complex128)

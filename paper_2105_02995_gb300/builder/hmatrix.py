@@ -87,12 +87,20 @@ class LowRankLevel:
     def add(self, c, J, U1, B, U2):
         self.blocks[(c, J)] = (U1, B, U2)
 
-    def apply(self, tree: Tree, lvl: int, X: np.ndarray, Y: np.ndarray):
-        """Y += A-hat_lvl X (both orientations of every stored pair)."""
+    def apply(self, tree: Tree, lvl: int, X: np.ndarray, Y: np.ndarray, live=None):
+        """Y += A-hat_lvl X (both orientations of every stored pair).  `live` (optional boolean
+        array over the cells of lvl) marks the cells where X may be nonzero; pairs with no live
+        cell contribute nothing and are skipped."""
         for (c, J), (U1, B, U2) in self.blocks.items():
+            lc = live is None or live[c]
+            lJ = live is None or live[J]
+            if not (lc or lJ):
+                continue
             pc, pJ = tree.points(lvl, c), tree.points(lvl, J)
-            Y[pJ] += U1 @ (B @ (U2.conj().T @ X[pc]))
-            Y[pc] += U2 @ (B.conj().T @ (U1.conj().T @ X[pJ]))
+            if lc:
+                Y[pJ] += U1 @ (B @ (U2.conj().T @ X[pc]))
+            if lJ:
+                Y[pc] += U2 @ (B.conj().T @ (U1.conj().T @ X[pJ]))
 
     def get(self, tree: Tree, lvl: int, X: int, Y: int, rows_pos: np.ndarray, cols_pos: np.ndarray):
         """Dense A[rows of X, cols of Y] for an admissible pair; *_pos are local positions."""
@@ -167,11 +175,16 @@ def peel(mv, geom: HGeometry, eps: float, seed: int = 20210506, s0: int = 24,
     abs_tol = eps * normA
     lowrank = {}
 
-    def subtract(X, upto):
+    def subtract(X, upto, cls=None, cls_lvl=None):
+        """sum_{l' <= upto} A-hat_l' X for a probe X supported on the cells `cls` of cls_lvl."""
         Y = np.zeros(X.shape, dtype=np.complex128)
         for lv in range(1, upto + 1):
             if lv in lowrank:
-                lowrank[lv].apply(tree, lv, X, Y)
+                live = None
+                if cls is not None:
+                    live = np.zeros(geom.beta ** lv, dtype=bool)
+                    live[np.asarray(cls) // geom.beta ** (cls_lvl - lv)] = True
+                lowrank[lv].apply(tree, lv, X, Y, live)
         return Y
 
     s = s0
@@ -190,7 +203,7 @@ def peel(mv, geom: HGeometry, eps: float, seed: int = 20210506, s0: int = 24,
                     G = _gauss(rng, (tree.size(lvl), s))
                     R[tree.points(lvl, c)] = G
                     Rc[c] = G
-                Y = mv(R) - subtract(R, lvl - 1)
+                Y = mv(R) - subtract(R, lvl - 1, cls, lvl)
                 for c in cls:
                     for J in il[c]:
                         Ysamp[(J, c)] = Y[tree.points(lvl, J)]
@@ -233,7 +246,7 @@ def peel(mv, geom: HGeometry, eps: float, seed: int = 20210506, s0: int = 24,
         R = np.zeros((N, m), dtype=np.complex128)
         for c in cls:
             R[tree.points(LH, c), np.arange(m)] = 1.0
-        Y = mv(R) - subtract(R, LH)
+        Y = mv(R) - subtract(R, LH, cls, LH)
         for c in cls:
             for J in geom.NL[LH][c]:
                 near[(J, c)] = Y[tree.points(LH, J)]  # A[points J, points c]
