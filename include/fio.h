@@ -153,6 +153,30 @@ int fio_launch_count(fio_op op, int which, int b, int* launches);
 int fio_apply_profiled(fio_op op, int which, const void* x, void* y, int64_t ld, int b, int dtype,
                        int precision, void* stream, float* stage_ms, int cap, int* nmarks);
 
+/* Size of the static device scratch used by fio_apply_inv_noalloc (64 MiB per device). */
+#define FIO_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* fio_apply_inv without any device allocation during the call.  (The paper has no counterpart:
+ * this entry point exists for callers, not for the method.)
+ *
+ * Who needs it: code that may not call cudaMalloc while it runs -- for example a caller whose
+ * device memory is owned by another allocator (a framework's caching allocator), or a latency-
+ * critical loop where the implicit device synchronisation of cudaMalloc/cudaFree is not
+ * acceptable.  fio_apply_inv may grow the operator's scratch pool on a larger b; this variant
+ * never allocates and never frees: its scratch is a static device array of
+ * FIO_NOALLOC_SCRATCH_BYTES that every device loading libfio holds until the process exits.
+ *
+ * Same arguments, result and errors as fio_apply_inv, plus: FIO_EINVAL when the call needs more
+ * scratch than the static array holds (3 work vectors of max_len x b elements, max_len the
+ * longest butterfly stage vector; e.g. the 1D N = 256 operator fits any b up to several
+ * thousand, the 2D n = 256 operator does not fit at b = 32).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  All calls share the one array, and its contents persist between
+ * calls: calls that overlap on the GPU (different streams, threads or operators) race and must
+ * be serialised by the caller.  Nothing in the array needs to start at zero. */
+int fio_apply_inv_noalloc(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
+                          int precision, void* stream);
+
 /* Free the device copies and scratch of op (synchronises the device first).  NULL is a no-op. */
 int fio_release(fio_op op);
 

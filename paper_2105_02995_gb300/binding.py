@@ -26,7 +26,7 @@ STATUS = {0: "FIO_OK", -1: "FIO_EINVAL", -2: "FIO_ENOMEM", -3: "FIO_EBADFACTORS"
           -4: "FIO_ENOCONV", -5: "FIO_ETIMEOUT", -6: "FIO_ECUDA", -7: "FIO_ENOTSUP"}
 SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv",
            "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_apply_profiled",
-           "fio_release", "fio_strerror"]
+           "fio_apply_inv_noalloc", "fio_release", "fio_strerror"]
 
 _lib = None
 
@@ -56,7 +56,8 @@ def load(path: str = LIB_PATH):
     lib = ctypes.CDLL(path)
     vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
     lib.fio_upload_factors.argtypes = [vp, ctypes.c_size_t, ctypes.c_uint, vp, ctypes.POINTER(vp)]
-    for name in ("fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv", "fio_apply_inv_host"):
+    for name in ("fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv", "fio_apply_inv_host",
+                 "fio_apply_inv_noalloc"):
         getattr(lib, name).argtypes = [vp, vp, vp, i64, c_int, c_int, c_int, vp]
     lib.fio_solve.argtypes = [vp, vp, vp, i64, c_int, c_int, ctypes.POINTER(SolveOpts),
                               ctypes.POINTER(SolveInfo), vp]

@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -524,4 +525,73 @@ extern "C" int fio_apply_profiled(fio_op op, int which, const void* x, void* y, 
   }
   for (auto& e : ev) cudaEventDestroy(e);
   return rc;
+}
+
+// ---------------------------------------------------------------------------------------------
+// fio_apply_inv_noalloc: the direct solve with scratch in a static device array
+// ---------------------------------------------------------------------------------------------
+// For callers that must not allocate device memory during a solve (see fio.h).  The scratch is
+// this file-scope array; every device that loads the library holds one copy until the process
+// exits.  Host code must not use the array's name as a device address: its address on the
+// current device comes from cudaGetSymbolAddress, taken once per device on the first call there.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FIO_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+void* g_noalloc_addr[kNoallocMaxDevices];
+std::mutex g_noalloc_mu;
+
+int noalloc_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FIO_ECUDA;
+  }
+  if (dev < 0 || dev >= kNoallocMaxDevices) return FIO_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return FIO_ECUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return FIO_OK;
+}
+
+template <typename V>
+void inv_with_buffers(fio_op op, const V* u, V* f, int64_t ld, int b, V* A, V* B, V* W,
+                      cudaStream_t s) {
+  bf_chain<V>(op, true, u, 1, ld, W, b, 1, b, A, B, s);
+  g_sweep<V>(op, W, A, b, s);
+  to_col<V>(W, f, ld, op->N, b, s);
+}
+}  // namespace
+
+extern "C" int fio_apply_inv_noalloc(fio_op op, const void* u, void* f, int64_t ld, int b,
+                                     int dtype, int precision, void* stream) {
+  int rc = check_args(op, u, f, ld, b, dtype, precision);
+  if (rc) return rc;
+  if (op->n_root == 0) return FIO_ENOTSUP;
+  if (b == 0) return FIO_OK;
+  const size_t es = precision == FIO_P64 ? sizeof(double2) : sizeof(float2);
+  const size_t per = (((size_t)op->max_len * (size_t)b * es) + 255) & ~(size_t)255;
+  if (per > FIO_NOALLOC_SCRATCH_BYTES / 3) return FIO_EINVAL;  // does not fit the static scratch
+  void* base = nullptr;
+  rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  if (cudaGetLastError() != cudaSuccess) return FIO_ECUDA;
+  uint8_t* p = (uint8_t*)base;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Nothing here needs clearing: every stage writes all of its outputs before a later stage
+  // reads them, so contents left by an earlier call are never read.
+  if (precision == FIO_P64)
+    inv_with_buffers<double2>(op, (const double2*)u, (double2*)f, ld, b, (double2*)p,
+                              (double2*)(p + per), (double2*)(p + 2 * per), s);
+  else
+    inv_with_buffers<float2>(op, (const float2*)u, (float2*)f, ld, b, (float2*)p,
+                             (float2*)(p + per), (float2*)(p + 2 * per), s);
+  return finish(s);
 }
