@@ -96,7 +96,8 @@ def build_operator(kind: str, n: int, eps_bf: float, eps_hif: float, L: int = No
     # 2D: K*K decays only slowly away from the diagonal, so an ID accuracy relative to each node's
     # own U-bar removes few DOFs; accept columns below eps ||A|| as well (the error that matters
     # for the inverse).  1D keeps the node-relative criterion.
-    hif_stages, hif = build_hif(H, eps_hif, tol_mode="global" if d == 2 else "local")
+    hif_stages, hif = build_hif(H, eps_hif, verbose=verbose,
+                                tol_mode="global" if d == 2 else "local")
     t3 = time.time()
     if verbose:
         print(f"[build] HIF: {t3 - t2:.1f} s, root {hif.root_size}, steps {hif.stats}", flush=True)

@@ -10,9 +10,10 @@ Structure (section 2, eq. for the nested bases and eq. for K-dot):
   * K-dot = U_L C_{L-1} ... C_h D H*_{L-h} ... H*_{L-1} V_L*.
 
 The middle-level blocks are compressed from sampled columns and rows (entries are evaluated on the
-fly; the whole of K is never formed): the column sample gives an orthonormal range basis Q, the
-row sample gives the coefficients by least squares on Q's sampled rows, and an SVD of the
-coefficients gives U D V*.  The sample grows until a fresh set of test entries agrees to eps.
+fly; the whole of K is never formed): a random column sample gives an orthonormal range basis Q,
+the rows a pivoted QR of Q* selects (plus random rows) give the coefficients by least squares on
+Q's sampled rows, and an SVD of the coefficients gives U D V*.  The sample grows until fresh
+whole rows and whole columns of the block agree to eps.
 This is the build's own construction (the paper uses an external code): any construction with the
 structure of the K-dot equation serves, and the result is checked against the dense K.
 
@@ -59,21 +60,28 @@ def lowrank_block(ent: FIOEntries, P: np.ndarray, Q: np.ndarray, eps: float,
     while True:
         sc, sr = min(n2, s), min(n1, s)
         c = np.sort(rng.choice(n2, sc, replace=False))
-        rho = np.sort(rng.choice(n1, sr, replace=False))
         Kc = ent.block(P, Q[c])
         Uc, svc, _ = np.linalg.svd(Kc, full_matrices=False)
         k1 = int(np.count_nonzero(svc > 1e-3 * eps * svc[0]))
         Qb = Uc[:, :k1]
+        # rows: the k1 rows a pivoted QR of Qb^* selects (they keep Qb[rho] well conditioned),
+        # plus random rows up to the sample size
+        piv = sla.qr(Qb.conj().T, mode="r", pivoting=True)[1][:k1]
+        extra = rng.choice(np.setdiff1d(np.arange(n1), piv), max(0, sr - k1), replace=False)
+        rho = np.sort(np.concatenate([piv, extra]).astype(np.int64))
         Kr = ent.block(P[rho], Q)
         X, *_ = sla.lstsq(Qb[rho], Kr, lapack_driver="gelsy")
         W, sv, Zh = np.linalg.svd(X, full_matrices=False)
         r = _rank(sv, eps)
         U, D, V = Qb @ W[:, :r], sv[:r], Zh[:r].conj().T
-        # fresh test entries
-        tr = rng.choice(n1, min(n1, 24), replace=False)
-        tc = rng.choice(n2, min(n2, 24), replace=False)
-        T = ent.block(P[tr], Q[tc])
-        err = np.linalg.norm(T - (U[tr] * D) @ V[tc].conj().T) / max(np.linalg.norm(T), 1e-300)
+        # validation on whole fresh rows and whole fresh columns (an error confined to a few
+        # directions shows up in full rows/columns, not necessarily in a small sub-block)
+        tr = rng.choice(n1, min(n1, 16), replace=False)
+        tc = rng.choice(n2, min(n2, 16), replace=False)
+        Tr = ent.block(P[tr], Q)
+        Tc = ent.block(P, Q[tc])
+        err = max(np.linalg.norm(Tr - (U[tr] * D) @ V.conj().T) / max(np.linalg.norm(Tr), 1e-300),
+                  np.linalg.norm(Tc - (U * D) @ V[tc].conj().T) / max(np.linalg.norm(Tc), 1e-300))
         enough = (k1 < sc - 8 or sc == n2) and (k1 < sr - 8 or sr == n1)
         if (enough and err < 10 * eps) or (sc == n2 and sr == n1):
             return U, D, V

@@ -58,6 +58,26 @@ def interp_decomp(Ub: np.ndarray, eps: float, ncols: int, abs_tol: float = 0.0):
     return P[:k], P[k:], T
 
 
+FALLBACKS = [0]
+
+
+def hpd_factor(A: np.ndarray):
+    """(L^{-1}, A^{-1}) for a Hermitian A = L L*.  Cholesky when A is numerically positive
+    definite; otherwise (approximation errors can push a tiny eigenvalue below zero) the
+    eigendecomposition with eigenvalues floored at 1e-12 max|lambda|, L = Q Lambda^{1/2}.  Any
+    square root serves: the node factor (Z E)* is stored densely."""
+    try:
+        L = np.linalg.cholesky(A)
+        Linv = sla.solve_triangular(L, np.eye(L.shape[0], dtype=np.complex128), lower=True)
+        return Linv, Linv.conj().T @ Linv
+    except np.linalg.LinAlgError:
+        FALLBACKS[0] += 1
+        lam, Q = np.linalg.eigh(A)
+        lam = np.maximum(lam, 1e-12 * np.max(np.abs(lam)))
+        Linv = (Q / np.sqrt(lam)).conj().T
+        return Linv, (Q / lam) @ Q.conj().T
+
+
 def eliminate(A: np.ndarray, red: np.ndarray, skel: np.ndarray, T: np.ndarray):
     """Zeroing + Gaussian elimination of the redundant DOFs of one node (eqs. Z, E).
 
@@ -71,9 +91,8 @@ def eliminate(A: np.ndarray, red: np.ndarray, skel: np.ndarray, T: np.ndarray):
     Asr_t = Asr - Ass @ T
     Arr_t = Arr - TH @ Asr - Asr.conj().T @ T + TH @ Ass @ T
     Arr_t = 0.5 * (Arr_t + Arr_t.conj().T)
-    L = np.linalg.cholesky(Arr_t)
-    Linv = sla.solve_triangular(L, np.eye(L.shape[0], dtype=np.complex128), lower=True)
-    W = sla.cho_solve((L, True), Asr_t.conj().T).conj().T  # A~_sr A~_rr^{-1}
+    Linv, Arr_inv = hpd_factor(Arr_t)
+    W = Asr_t @ Arr_inv  # A~_sr A~_rr^{-1}
     schur = Ass - W @ Asr_t.conj().T
     schur = 0.5 * (schur + schur.conj().T)
     nr, ns = len(red), len(skel)
@@ -138,18 +157,27 @@ class HIF:
                                        self.t.pos[rows] - X * size, self.t.pos[cols] - Y * size)
 
     # ---- driver ----------------------------------------------------------------------------
-    def run(self):
+    def run(self, verbose: bool = False):
+        import time
         g, t = self.g, self.t
         LH = g.LH
         self.dofs = {c: t.points(LH, c).copy() for c in range(g.beta ** LH)}
         self.near = {k: v.copy() for k, v in self.H.near.items()}
+        t0 = time.time()
         for lvl in range(LH, self.stop - 1, -1):
             self._cells(lvl)
             if self.edges and lvl >= 2:
                 self._edges(lvl)
             if lvl > self.stop:
                 self._merge(lvl)
+            if verbose:
+                print(f"[build]   HIF level {lvl}: {time.time() - t0:.1f} s, active "
+                      f"{sum(len(v) for v in self.dofs.values())}", flush=True)
         self._root(self.stop)
+        if verbose:
+            print(f"[build]   HIF root {self.root_size}: {time.time() - t0:.1f} s, "
+                  f"eigen fallbacks {FALLBACKS[0]}", flush=True)
+        self.fallbacks = FALLBACKS[0]
         return self.stages
 
     def _restrict(self, c: int, keep_pos: np.ndarray, lvl: int):
@@ -374,8 +402,7 @@ class HIF:
         if cells:
             A0 = np.block(rows)
             A0 = 0.5 * (A0 + A0.conj().T)
-            L = np.linalg.cholesky(A0)
-            A0inv = sla.cho_solve((L, True), np.eye(len(S0), dtype=np.complex128))
+            _, A0inv = hpd_factor(A0)
             A0inv = 0.5 * (A0inv + A0inv.conj().T)
             st.add(A0inv, S0, S0)
         self.root_size = len(S0)
@@ -394,6 +421,6 @@ class HIF:
         raise RuntimeError("cells neither near nor admissible")
 
 
-def build_hif(H: HMatrix, eps: float, **kw):
+def build_hif(H: HMatrix, eps: float, verbose: bool = False, **kw):
     h = HIF(H, eps, **kw)
-    return h.run(), h
+    return h.run(verbose), h

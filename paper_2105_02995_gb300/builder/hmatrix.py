@@ -23,8 +23,11 @@ A is reached only through a product callable mv(X) = K-dot* (K-dot X).
 
 from __future__ import annotations
 
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
+from . import blas
 from .geometry import Tree
 
 
@@ -208,31 +211,35 @@ def peel(mv, geom: HGeometry, eps: float, seed: int = 20210506, s0: int = 24,
                     for J in il[c]:
                         Ysamp[(J, c)] = Y[tree.points(lvl, J)]
             lr = LowRankLevel()
-            saturated = False
-            for c in range(geom.beta ** lvl):
-                for J in il[c]:
-                    if J <= c:
-                        continue
-                    Y1 = Ysamp[(J, c)]  # A_Jc R_c
-                    Y2 = Ysamp[(c, J)]  # A_cJ R_J = A_Jc^* R_J
-                    # directions of A_Jc above ~abs_tol/10 show up in A_Jc R above ~abs_tol/10 sqrt(s)
-                    U1 = _orth(Y1, 0.1 * abs_tol * np.sqrt(s))
-                    U2 = _orth(Y2, 0.1 * abs_tol * np.sqrt(s))
-                    if U1.shape[1] == 0 or U2.shape[1] == 0:
-                        continue
-                    if max(U1.shape[1], U2.shape[1]) > s - 10 and s < s_max:
-                        saturated = True
-                        break
-                    core = Rc[J].conj().T @ Y1  # R_J^* A_Jc R_c
-                    B = np.linalg.pinv(Rc[J].conj().T @ U1, rcond=1e-12) @ core @ \
-                        np.linalg.pinv(U2.conj().T @ Rc[c], rcond=1e-12)
-                    W, sv, Zh = np.linalg.svd(B, full_matrices=False)
-                    r = int(np.count_nonzero(sv > abs_tol))
-                    if r == 0:
-                        continue
-                    lr.add(c, J, U1 @ W[:, :r], np.diag(sv[:r]), U2 @ Zh[:r].conj().T)
-                if saturated:
-                    break
+            pairs = [(c, J) for c in range(geom.beta ** lvl) for J in il[c] if J > c]
+
+            def one(cJ, s=s, Ysamp=Ysamp, Rc=Rc):
+                c, J = cJ
+                Y1 = Ysamp[(J, c)]  # A_Jc R_c
+                Y2 = Ysamp[(c, J)]  # A_cJ R_J = A_Jc^* R_J
+                # directions of A_Jc above ~abs_tol/10 show up in A_Jc R above ~abs_tol/10 sqrt(s)
+                U1 = _orth(Y1, 0.1 * abs_tol * np.sqrt(s))
+                U2 = _orth(Y2, 0.1 * abs_tol * np.sqrt(s))
+                if U1.shape[1] == 0 or U2.shape[1] == 0:
+                    return None
+                if max(U1.shape[1], U2.shape[1]) > s - 10 and s < s_max:
+                    return "saturated"
+                core = Rc[J].conj().T @ Y1  # R_J^* A_Jc R_c
+                B = np.linalg.pinv(Rc[J].conj().T @ U1, rcond=1e-12) @ core @ \
+                    np.linalg.pinv(U2.conj().T @ Rc[c], rcond=1e-12)
+                W, sv, Zh = np.linalg.svd(B, full_matrices=False)
+                r = int(np.count_nonzero(sv > abs_tol))
+                if r == 0:
+                    return None
+                return (c, J, U1 @ W[:, :r], np.diag(sv[:r]), U2 @ Zh[:r].conj().T)
+
+            with blas.threads(1), ThreadPoolExecutor(blas.pool_workers()) as ex:
+                results = list(ex.map(one, pairs))
+            saturated = any(isinstance(x, str) for x in results)
+            if not saturated:
+                for res in results:
+                    if res is not None:
+                        lr.add(*res)
             if saturated:
                 s = min(2 * s, s_max)
                 continue

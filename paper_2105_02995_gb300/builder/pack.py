@@ -33,6 +33,8 @@ def checksum(buf, start: int, end: int) -> int:
 
 def _stage_arrays(st: Stage):
     R, C = st.padded_shape()
+    # even padded widths keep every block row 16-byte aligned in the complex64 copy
+    R, C = R + (R & 1), C + (C & 1)
     nb = len(st.blocks)
     M = np.zeros((nb, R, C), dtype="<c16")
     ii = np.full((nb, C), -1, dtype="<i4")

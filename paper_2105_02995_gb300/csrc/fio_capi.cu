@@ -18,6 +18,7 @@ using namespace fio;
 namespace {
 
 constexpr size_t kHeader = 256;
+constexpr int kTileRows = 64;  // output rows per CTA of every k_stage_mm / k_stage_mm_pipe shape
 constexpr size_t kStageBytes = 64;
 
 template <typename T>
@@ -141,7 +142,50 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
     op->st.push_back(st);
   }
 
+  // per block: extent of the valid rows / columns; CTA tile lists (64-row tiles) per direction
+  std::vector<int2> meta;
+  std::vector<size_t> mdims(nst), mfwd(nst), madj(nst);
+  for (uint64_t si = 0; si < nst; ++si) {
+    fio::Stage& st = op->st[si];
+    const int32_t* ii = (const int32_t*)(p + st.offIn);
+    const int32_t* oo = (const int32_t*)(p + st.offOut);
+    mdims[si] = meta.size();
+    for (uint32_t b = 0; b < st.nblk; ++b) {
+      int rb = 0, cb = 0;
+      for (uint32_t r = 0; r < st.R; ++r)
+        if (oo[(size_t)b * st.R + r] >= 0) rb = (int)r + 1;
+      for (uint32_t c = 0; c < st.C; ++c)
+        if (ii[(size_t)b * st.C + c] >= 0) cb = (int)c + 1;
+      meta.push_back(make_int2(rb, cb));
+    }
+    mfwd[si] = meta.size();
+    for (uint32_t b = 0; b < st.nblk; ++b)
+      for (int t = 0; t * kTileRows < meta[mdims[si] + b].x; ++t) meta.push_back(make_int2((int)b, t));
+    st.ntiles_fwd = (int)(meta.size() - mfwd[si]);
+    madj[si] = meta.size();
+    for (uint32_t b = 0; b < st.nblk; ++b)
+      for (int t = 0; t * kTileRows < meta[mdims[si] + b].y; ++t) meta.push_back(make_int2((int)b, t));
+    st.ntiles_adj = (int)(meta.size() - madj[si]);
+  }
+
   cudaStream_t s = (cudaStream_t)stream;
+  if (!meta.empty()) {
+    if (cudaMalloc(&op->meta, meta.size() * sizeof(int2)) != cudaSuccess) {
+      cudaGetLastError();
+      delete op;
+      return FIO_ENOMEM;
+    }
+    op->meta_bytes = meta.size() * sizeof(int2);
+    if (cudaMemcpy(op->meta, meta.data(), op->meta_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      fio_release(op);
+      return FIO_ECUDA;
+    }
+    for (uint64_t si = 0; si < nst; ++si) {
+      op->st[si].dims = (const int2*)op->meta + mdims[si];
+      op->st[si].tiles_fwd = (const int2*)op->meta + mfwd[si];
+      op->st[si].tiles_adj = (const int2*)op->meta + madj[si];
+    }
+  }
   if (cudaMalloc(&op->arena, nbytes) != cudaSuccess) {
     cudaGetLastError();
     delete op;
@@ -192,6 +236,7 @@ extern "C" int fio_release(fio_op op) {
   cudaDeviceSynchronize();
   if (op->arena) cudaFree(op->arena);
   if (op->arena32) cudaFree(op->arena32);
+  if (op->meta) cudaFree(op->meta);
   if (op->scratch) cudaFree(op->scratch);
   fio_solver_free(op);
   cudaGetLastError();
@@ -204,7 +249,8 @@ extern "C" int fio_query(fio_op op, int* d, int64_t* n, int64_t* N, size_t* devi
   if (d) *d = op->d;
   if (n) *n = op->n;
   if (N) *N = op->N;
-  if (device_bytes) *device_bytes = op->arena_bytes + op->arena32_bytes + op->scratch_bytes + op->solver_bytes;
+  if (device_bytes)
+    *device_bytes = op->arena_bytes + op->arena32_bytes + op->meta_bytes + op->scratch_bytes + op->solver_bytes;
   return FIO_OK;
 }
 
@@ -275,14 +321,50 @@ template <> struct ChunkK<float2> { static constexpr int v = 32; };
 template <typename V, bool ADJ, int TX, int TB, int TR>
 void launch_mm(StageArgs<V> a, cudaStream_t s) {
   constexpr int RT = (256 / TX) * TR, BT = TX * TB;
+  static_assert(RT == kTileRows, "tile lists are built for 64-row tiles");
   const int nrows = ADJ ? a.C : a.R;
   a.ntiles = (nrows + RT - 1) / RT;
-  dim3 grid((unsigned)(a.nblk * a.ntiles), (unsigned)((a.b + BT - 1) / BT));
+  const long long ncta = a.tiles ? a.ntiles_list : (long long)a.nblk * a.ntiles;
+  if (ncta == 0) return;
+  dim3 grid((unsigned)ncta, (unsigned)((a.b + BT - 1) / BT));
   k_stage_mm<V, ADJ, TX, TB, TR, ChunkK<V>::v><<<grid, 256, 0, s>>>(a);
+}
+
+template <typename V, bool ADJ, int TX, int TB, int TR>
+void launch_pipe(StageArgs<V> a, cudaStream_t s) {
+  constexpr int CK = ChunkK<V>::v;
+  using S = PipeShape<V, ADJ, TX, TB, TR, CK>;
+  static bool attr = false;  // one attribute call per instantiation (host-side, idempotent)
+  if (!attr) {
+    cudaFuncSetAttribute(k_stage_mm_pipe<V, ADJ, TX, TB, TR, CK>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    attr = true;
+  }
+  static_assert(S::RT == kTileRows, "tile lists are built for 64-row tiles");
+  const int nrows = ADJ ? a.C : a.R;
+  a.ntiles = (nrows + S::RT - 1) / S::RT;
+  const long long ncta = a.tiles ? a.ntiles_list : (long long)a.nblk * a.ntiles;
+  if (ncta == 0) return;
+  dim3 grid((unsigned)ncta, (unsigned)((a.b + S::BT - 1) / S::BT));
+  k_stage_mm_pipe<V, ADJ, TX, TB, TR, CK><<<grid, 256, S::SMEM, s>>>(a);
+}
+
+// the pipelined kernel needs row-major x with 16-byte aligned rows of M and of x
+template <typename V>
+bool pipe_ok(const StageArgs<V>& a) {
+  const int vpc = 16 / (int)sizeof(V);
+  return a.xcs == 1 && a.xrs == a.b && a.C % vpc == 0 && a.b % vpc == 0 &&
+         ((uintptr_t)a.M & 15) == 0 && ((uintptr_t)a.x & 15) == 0;
 }
 
 template <typename V, bool ADJ>
 void launch_stage_dir(const StageArgs<V>& a, cudaStream_t s) {
+  if (a.b >= 5 && pipe_ok(a)) {
+    if (a.b <= 8) launch_pipe<V, ADJ, 8, 1, 2>(a, s);
+    else if (a.b <= 16) launch_pipe<V, ADJ, 16, 1, 4>(a, s);
+    else launch_pipe<V, ADJ, 16, 2, 4>(a, s);
+    return;
+  }
   if (a.b <= 4) {
     if (!ADJ) {
       const long long warps = (long long)a.nblk * a.R;
@@ -320,6 +402,9 @@ void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long lon
   a.ycs = ycs;
   a.b = b;
   a.ntiles = 1;
+  a.dims = st.dims;
+  a.tiles = adj ? st.tiles_adj : st.tiles_fwd;
+  a.ntiles_list = adj ? st.ntiles_adj : st.ntiles_fwd;
   if (adj) launch_stage_dir<V, true>(a, s);
   else launch_stage_dir<V, false>(a, s);
 }
@@ -335,6 +420,19 @@ void inplace_stage(const Stage& st, bool adj, V* W, V* S, int b, cudaStream_t s)
   mark(s);
 }
 
+template <typename V>
+void to_row(const V* X, long long ld, V* W, long long N, int b, cudaStream_t s) {
+  dim3 grid((unsigned)((N + 31) / 32), (unsigned)((b + 31) / 32));
+  k_col_to_row<V><<<grid, dim3(32, 8), 0, s>>>(X, ld, W, N, b);
+  mark(s);
+}
+template <typename V>
+void to_col(const V* W, V* Y, long long ld, long long N, int b, cudaStream_t s) {
+  dim3 grid((unsigned)((N + 31) / 32), (unsigned)((b + 31) / 32));
+  k_row_to_col<V><<<grid, dim3(32, 8), 0, s>>>(W, Y, ld, N, b);
+  mark(s);
+}
+
 // K-dot (adj = false) or K-dot* (adj = true): x (xrs, xcs) -> y (yrs, ycs); A, B ping-pong
 template <typename V>
 void bf_chain(fio_op op, bool adj, const V* x, long long xrs, long long xcs, V* y, long long yrs,
@@ -342,6 +440,13 @@ void bf_chain(fio_op op, bool adj, const V* x, long long xrs, long long xcs, V* 
   const int n = op->n_bf;
   const V* cur = x;
   long long crs = xrs, ccs = xcs;
+  if (b >= 5 && xrs == 1 && n > 1) {
+    // caller's column-major input -> row-major work array, so every stage streams whole rows
+    to_row<V>(x, xcs, B, op->N, b, s);
+    cur = B;
+    crs = b;
+    ccs = 1;
+  }
   for (int k = 0; k < n; ++k) {
     const Stage& st = op->st[adj ? n - 1 - k : k];
     const bool last = k == n - 1;
@@ -362,19 +467,6 @@ void g_sweep(fio_op op, V* W, V* S, int b, cudaStream_t s) {
   for (int t = 0; t < nh; ++t) inplace_stage<V>(op->st[h0 + t], false, W, S, b, s);
   for (int t = 0; t < op->n_root; ++t) inplace_stage<V>(op->st[h0 + nh + t], false, W, S, b, s);
   for (int t = nh - 1; t >= 0; --t) inplace_stage<V>(op->st[h0 + t], true, W, S, b, s);
-}
-
-template <typename V>
-void to_row(const V* X, long long ld, V* W, long long N, int b, cudaStream_t s) {
-  dim3 grid((unsigned)((N + 31) / 32), (unsigned)((b + 31) / 32));
-  k_col_to_row<V><<<grid, dim3(32, 8), 0, s>>>(X, ld, W, N, b);
-  mark(s);
-}
-template <typename V>
-void to_col(const V* W, V* Y, long long ld, long long N, int b, cudaStream_t s) {
-  dim3 grid((unsigned)((N + 31) / 32), (unsigned)((b + 31) / 32));
-  k_row_to_col<V><<<grid, dim3(32, 8), 0, s>>>(W, Y, ld, N, b);
-  mark(s);
 }
 
 int check_args(fio_op op, const void* x, const void* y, int64_t ld, int b, int dtype, int prec) {

@@ -20,6 +20,12 @@ struct Stage {
   const int* in = nullptr;       // device
   const int* out = nullptr;      // device
   long long launch_rows;
+  // per block: valid rows / columns (the padded tail of a block is never touched), and the CTA
+  // work lists of 64-row tiles for the forward (over rows) and adjoint (over columns) directions
+  const int2* dims = nullptr;      // device, nblk x (rows, cols)
+  const int2* tiles_fwd = nullptr;  // device, (block, tile) pairs
+  const int2* tiles_adj = nullptr;
+  int ntiles_fwd = 0, ntiles_adj = 0;
 };
 
 }  // namespace fio
@@ -37,6 +43,8 @@ struct fio_op_s {
   size_t arena32_bytes = 0;
   void* scratch = nullptr;        // 5 work arrays of max_len x b (grown on demand)
   size_t scratch_bytes = 0;
+  void* meta = nullptr;           // per-block dims and tile lists of every stage
+  size_t meta_bytes = 0;
   void* solver = nullptr;         // solver work arrays (fio_solve.cu)
   size_t solver_bytes = 0;
 };

@@ -57,8 +57,32 @@ struct StageArgs {
   V* y;
   long long yrs, ycs;
   int b;
-  int ntiles;        // output-row tiles per block
+  int ntiles;        // output-row tiles per block (when tiles == nullptr)
+  const int2* dims;  // per block (valid rows, valid cols), or nullptr: the padded R x C
+  const int2* tiles; // per CTA (block, 64-row tile), or nullptr: blockIdx.x = blk * ntiles + tile
+  int ntiles_list;   // length of `tiles`
 };
+
+// block, row tile and valid extent of the CTA; rows/cols are in the direction of the product
+template <typename V, bool ADJ>
+__device__ __forceinline__ void cta_work(const StageArgs<V>& a, int& blk, int& tile, int& Rb, int& Cb) {
+  if (a.tiles) {
+    const int2 t = a.tiles[blockIdx.x];
+    blk = t.x;
+    tile = t.y;
+  } else {
+    blk = blockIdx.x / a.ntiles;
+    tile = blockIdx.x - blk * a.ntiles;
+  }
+  if (a.dims) {
+    const int2 d = a.dims[blk];
+    Rb = d.x;
+    Cb = d.y;
+  } else {
+    Rb = a.R;
+    Cb = a.C;
+  }
+}
 
 template <typename V, bool ADJ, int TX, int TB, int TR, int CK>
 __global__ void __launch_bounds__(256) k_stage_mm(StageArgs<V> a) {
@@ -68,11 +92,11 @@ __global__ void __launch_bounds__(256) k_stage_mm(StageArgs<V> a) {
   __shared__ V sM[CK][RT + 1];
   __shared__ V sX[CK][BT];
 
-  const int blk = blockIdx.x / a.ntiles;
-  const int tile = blockIdx.x - blk * a.ntiles;
+  int blk, tile, Rb, Cb;
+  cta_work<V, ADJ>(a, blk, tile, Rb, Cb);
   const int j0 = blockIdx.y * BT;
-  const int nrows = ADJ ? a.C : a.R;
-  const int ncols = ADJ ? a.R : a.C;
+  const int nrows = ADJ ? Cb : Rb;
+  const int ncols = ADJ ? Rb : Cb;
   const V* M = a.M + (size_t)blk * a.R * a.C;
   const int* rowidx = ADJ ? a.in + (size_t)blk * a.C : a.out + (size_t)blk * a.R;
   const int* colidx = ADJ ? a.out + (size_t)blk * a.R : a.in + (size_t)blk * a.C;
@@ -145,6 +169,124 @@ __global__ void __launch_bounds__(256) k_stage_mm(StageArgs<V> a) {
   }
 }
 
+// ---- pipelined variant: 16-byte cp.async copies, two shared-memory buffers --------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Same contract as k_stage_mm, for the internal row-major vectors (xrs = b, xcs = 1) with every
+// copied row 16-byte aligned (C * sizeof(V) and b * sizeof(V) multiples of 16).  Chunk k+1 of the
+// block's columns (its M tile and its gathered x rows) is in flight while chunk k is multiplied;
+// out-of-range and padding copies are zero-filled (source size 0).  Dynamic shared memory:
+// 2 * (MROWS * MLD + CK * BT) * sizeof(V).
+template <typename V, bool ADJ, int TX, int TB, int TR, int CK>
+struct PipeShape {
+  static constexpr int TY = 256 / TX, RT = TY * TR, BT = TX * TB;
+  static constexpr int VPC = 16 / (int)sizeof(V);  // complex values per 16-byte copy
+  static constexpr int MROWS = ADJ ? CK : RT, MCOLS = ADJ ? RT : CK, MLD = MCOLS + VPC;
+  static constexpr int SMEM = 2 * (MROWS * MLD + CK * BT) * (int)sizeof(V);
+};
+
+template <typename V, bool ADJ, int TX, int TB, int TR, int CK>
+__global__ void __launch_bounds__(256) k_stage_mm_pipe(StageArgs<V> a) {
+  using S = PipeShape<V, ADJ, TX, TB, TR, CK>;
+  constexpr int TY = S::TY, RT = S::RT, BT = S::BT, VPC = S::VPC;
+  constexpr int MROWS = S::MROWS, MCOLS = S::MCOLS, MLD = S::MLD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sM = reinterpret_cast<V*>(smem_raw);
+  V* sX = sM + 2 * MROWS * MLD;
+
+  int blk, tile, Rb, Cb;
+  cta_work<V, ADJ>(a, blk, tile, Rb, Cb);
+  const int j0 = blockIdx.y * BT;
+  const int nrows = ADJ ? Cb : Rb;
+  const int ncols = ADJ ? Rb : Cb;
+  const V* M = a.M + (size_t)blk * a.R * a.C;
+  const int* rowidx = ADJ ? a.in + (size_t)blk * a.C : a.out + (size_t)blk * a.R;
+  const int* colidx = ADJ ? a.out + (size_t)blk * a.R : a.in + (size_t)blk * a.C;
+  const int r0 = tile * RT;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX;
+  const int ty = tid / TX;
+
+  auto load = [&](int buf, int c0) {
+    V* dM = sM + buf * MROWS * MLD;
+    constexpr int CPR = MCOLS / VPC;
+    for (int e = tid; e < MROWS * CPR; e += 256) {
+      const int mr = e / CPR;
+      const int mc = (e - mr * CPR) * VPC;
+      const int grow = (ADJ ? c0 : r0) + mr;  // row of M
+      const int gcol = (ADJ ? r0 : c0) + mc;  // column of M (a 16-byte chunk may end in the
+                                              // zero padding of the stored row, never beyond it)
+      const bool ok = grow < Rb && gcol < Cb;
+      cp_async16(dM + mr * MLD + mc, ok ? (const void*)(M + (size_t)grow * a.C + gcol) : (const void*)M,
+                 ok ? 16 : 0);
+    }
+    V* dX = sX + buf * CK * BT;
+    constexpr int CPX = BT / VPC;
+    for (int e = tid; e < CK * CPX; e += 256) {
+      const int cc = e / CPX;
+      const int jj = (e - cc * CPX) * VPC;
+      const int c = c0 + cc, j = j0 + jj;
+      const int idx = c < ncols ? colidx[c] : -1;
+      const bool ok = idx >= 0 && j < a.b;
+      cp_async16(dX + cc * BT + jj, ok ? (const void*)(a.x + (long long)idx * a.xrs + j) : (const void*)a.x,
+                 ok ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+
+  V acc[TR][TB];
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int k = 0; k < TB; ++k) acc[i][k] = czero<V>();
+
+  const int nchunks = (ncols + CK - 1) / CK;
+  load(0, 0);
+  for (int k = 0; k < nchunks; ++k) {
+    if (k + 1 < nchunks) {
+      load((k + 1) & 1, (k + 1) * CK);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const V* tM = sM + (k & 1) * MROWS * MLD;
+    const V* tX = sX + (k & 1) * CK * BT;
+#pragma unroll 8
+    for (int cc = 0; cc < CK; ++cc) {
+      V m[TR], xv[TB];
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+        m[i] = ADJ ? cconj(tM[cc * MLD + ty + TY * i]) : tM[(ty + TY * i) * MLD + cc];
+#pragma unroll
+      for (int q = 0; q < TB; ++q) xv[q] = tX[cc * BT + tx + TX * q];
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int q = 0; q < TB; ++q) acc[i][q] = cmac(acc[i][q], m[i], xv[q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TR; ++i) {
+    const int r = r0 + ty + TY * i;
+    if (r >= nrows) continue;
+    const int idx = rowidx[r];
+    if (idx < 0) continue;
+#pragma unroll
+    for (int q = 0; q < TB; ++q) {
+      const int j = j0 + tx + TX * q;
+      if (j < a.b) a.y[(long long)idx * a.yrs + (long long)j * a.ycs] = acc[i][q];
+    }
+  }
+}
+
 // forward streaming matvec: one warp per block row, b <= 4
 template <typename V>
 __global__ void __launch_bounds__(256) k_stage_mv_fwd(StageArgs<V> a) {
@@ -154,12 +296,15 @@ __global__ void __launch_bounds__(256) k_stage_mv_fwd(StageArgs<V> a) {
   if (warp >= total) return;
   const int blk = warp / a.R;
   const int r = warp - blk * a.R;
+  const int Rb = a.dims ? a.dims[blk].x : a.R;
+  const int Cb = a.dims ? a.dims[blk].y : a.C;
+  if (r >= Rb) return;
   const int oidx = a.out[(size_t)blk * a.R + r];
   if (oidx < 0) return;
   const V* Mr = a.M + ((size_t)blk * a.R + r) * a.C;
   const int* in = a.in + (size_t)blk * a.C;
   V acc[4] = {czero<V>(), czero<V>(), czero<V>(), czero<V>()};
-  for (int c = lane; c < a.C; c += 32) {
+  for (int c = lane; c < Cb; c += 32) {
     const int ic = in[c];
     if (ic < 0) continue;
     const V m = Mr[c];
@@ -185,13 +330,15 @@ template <typename V>
 __global__ void __launch_bounds__(256) k_stage_mv_adj(StageArgs<V> a) {
   const int blk = blockIdx.y;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= a.C) return;
+  const int Rb = a.dims ? a.dims[blk].x : a.R;
+  const int Cb = a.dims ? a.dims[blk].y : a.C;
+  if (c >= Cb) return;
   const int ic = a.in[(size_t)blk * a.C + c];
   if (ic < 0) return;
   const V* M = a.M + (size_t)blk * a.R * a.C + c;
   const int* out = a.out + (size_t)blk * a.R;
   V acc[4] = {czero<V>(), czero<V>(), czero<V>(), czero<V>()};
-  for (int r = 0; r < a.R; ++r) {
+  for (int r = 0; r < Rb; ++r) {
     const int orow = out[r];
     if (orow < 0) continue;
     const V m = cconj(M[(size_t)r * a.C]);

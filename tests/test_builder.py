@@ -101,3 +101,19 @@ def test_hmatrix_matches_normal_matrix():
     H = peel(lambda X: A @ X, HGeometry(1, 256, 3), 1e-6)
     Sd = H.apply(np.eye(256, dtype=complex))
     assert spec(A - Sd) / spec(A) < 5e-6
+
+
+def test_butterfly_sampled_path_large_N():
+    """N = 16384 uses the sampled middle-level construction (blocks too large for a full SVD):
+    K-dot against the oracle's K at sampled rows, relative error within a few eps_BF.  (A random
+    row sample once made one block's coefficient solve ill-conditioned; full rows catch that.)"""
+    from paper_2105_02995_gb300.builder import PaddedStages
+    N, eps = 16384, 1e-7
+    st, _ = build_butterfly("ex1", N, 10, eps)
+    ps = PaddedStages(st)
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((N, 2)) + 1j * rng.standard_normal((N, 2))
+    rows = np.sort(rng.choice(N, 48, replace=False))
+    got = ps.apply(f)[rows]
+    want = fo.K_rows(fo.FIO("ex1", N), rows, f)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 5 * eps
