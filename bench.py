@@ -249,7 +249,9 @@ def main():
     tot = totals(buf)
     st = tot["stages"]
     nbf = tot["n_bf"]
-    groups = []  # (label, stage dict or None, direction)
+    groups = []  # (label, stage dict or None), in the order fio_apply_profiled marks them
+    if b >= 5 and nbf > 1:
+        groups.append(("layout", None))  # caller's column-major u -> row-major work array
     for s in reversed(range(nbf)):
         groups.append(("bf", st[s]))
     hif = st[nbf:]
