@@ -291,6 +291,26 @@ def main():
                          "peak_gbs": peaks.get("hbm_gbs"), "peak_source": src},
             "stage_ms_sum": round(kern_time, 4), "step_ms": round(ms, 4)}
 
+    # tensor-core stage products (tcgen05, TF32 / BF16 operands, FP32 accumulation), same timing
+    variants = {}
+    for name, prec in (("tf32_tensor_core", binding.FIO_PTF32), ("bf16_tensor_core", binding.FIO_PBF16)):
+        try:
+            for _ in range(3):
+                op.apply_inv(u, f, precision=prec)
+            torch.cuda.synchronize()
+            evv = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(a.steps)]
+            for k in range(a.steps):
+                flush.fill_(float(k))
+                evv[k][0].record(stream)
+                op.apply_inv(u, f, precision=prec)
+                evv[k][1].record(stream)
+            torch.cuda.synchronize()
+            vms = allmax(ws, statistics.mean(s_.elapsed_time(e_) for s_, e_ in evv))
+            variants[name] = {"value": round(ws * b * 1000.0 / vms, 2), "unit": "RHS/s", "ms_per_step": round(vms, 4)}
+        except Exception as exc:  # reported, not hidden: the variant line says why it is missing
+            variants[name] = {"error": str(exc)[:200]}
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     uh = torch.from_numpy(u_np.astype(np.complex64)).t().contiguous().pin_memory()  # (b, N) rows = RHS
     fh = torch.empty_like(uh).pin_memory()
@@ -316,7 +336,7 @@ def main():
                 "data": "synthetic", "config": config_of(a, info, "flushed before every step (256 MB write)"),
                 "rhs_N_per_s": round(value * N, 1), "wall_ms_per_step": round(1000 * t_wall / a.steps, 4),
                 "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-                "cpu_baseline": cpu, "stages": stage_rows,
+                "cpu_baseline": cpu, "stages": stage_rows, "variants": variants,
                 "factors": {"P_K": tot["P_K"], "P_G": tot["P_G"], "padded_K": tot["padded_K"],
                             "padded_G": tot["padded_G"], "bytes_c64": 8 * (tot["padded_K"] + tot["padded_G"]),
                             "build_s": {k: info.get(k) for k in ("t_bf", "t_peel", "t_hif", "t_total")}}}

@@ -19,8 +19,13 @@
  * not overlap.  b >= 0; b == 0 is a no-op.
  *
  * PRECISION.  FIO_P64 applies the FP64 (complex128) copy of the factors, FIO_P32 the FP32
- * (complex64) copy, which fio_upload_factors derives on the device.  The vector dtype must match
- * the precision (C128 with P64, C64 with P32); other pairs return FIO_EINVAL.
+ * (complex64) copy, which fio_upload_factors derives on the device (FP32 CUDA-core arithmetic).
+ * FIO_PTF32 and FIO_PBF16 run the stage products on the tensor cores (tcgen05) with FP32
+ * accumulation: TF32 products of the complex64 copy, or products of a bfloat16 copy of the
+ * factors with bfloat16-rounded vectors; both take complex64 vectors and are meant as the inner
+ * precision of an iterative refinement (their rounding is ~1e-3 resp. ~4e-3 per stage).  With
+ * fewer than 8 right-hand sides they fall back to the FP32 CUDA-core kernels.  The vector dtype
+ * must match the precision (C128 with P64, C64 with the others); other pairs return FIO_EINVAL.
  *
  * STREAMS AND SCRATCH.  Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
  * default stream) unless stated otherwise.  Each operator owns a scratch pool (device memory for
@@ -78,11 +83,12 @@ extern "C" {
 typedef struct fio_op_s* fio_op;
 
 typedef enum { FIO_C128 = 0, FIO_C64 = 1 } fio_dtype;
-typedef enum { FIO_P64 = 0, FIO_P32 = 1 } fio_precision;
+typedef enum { FIO_P64 = 0, FIO_P32 = 1, FIO_PTF32 = 2, FIO_PBF16 = 3 } fio_precision;
 typedef enum { FIO_DIRECT = 0, FIO_PCG = 1, FIO_GMRES = 2, FIO_IR = 3 } fio_method;
 
 #define FIO_MASK_P64 1u
 #define FIO_MASK_P32 2u
+#define FIO_MASK_TC 4u /* tensor-core copies: block-transposed complex64 and bf16 (both orientations) */
 
 typedef struct {
   int method;    /* fio_method                                                                 */

@@ -19,9 +19,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfio.so")
 
 FIO_C128, FIO_C64 = 0, 1
-FIO_P64, FIO_P32 = 0, 1
+FIO_P64, FIO_P32, FIO_PTF32, FIO_PBF16 = 0, 1, 2, 3
 FIO_DIRECT, FIO_PCG, FIO_GMRES, FIO_IR = 0, 1, 2, 3
-FIO_MASK_P64, FIO_MASK_P32 = 1, 2
+FIO_MASK_P64, FIO_MASK_P32, FIO_MASK_TC = 1, 2, 4
 STATUS = {0: "FIO_OK", -1: "FIO_EINVAL", -2: "FIO_ENOMEM", -3: "FIO_EBADFACTORS",
           -4: "FIO_ENOCONV", -5: "FIO_ETIMEOUT", -6: "FIO_ECUDA", -7: "FIO_ENOTSUP"}
 SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv",
@@ -138,7 +138,7 @@ class Operator:
         _check(self._lib.fio_launch_count(self.h, k, b, ctypes.byref(out)), "fio_launch_count")
         return out.value
 
-    def _apply(self, fn, name, x, y):
+    def _apply(self, fn, name, x, y, precision=None):
         import torch
         if y is None:
             y = torch.empty_like(colmajor(x) if x.dim() == 2 else x)
@@ -147,14 +147,18 @@ class Operator:
         dty, precy, by, ldy = _vec(y, self.N)
         if (dt, b) != (dty, by) or ld != ldy:
             raise ValueError("x and y must have the same dtype, shape and leading dimension")
+        if precision is not None:
+            prec = precision
         _check(fn(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), ld, b, dt,
                   prec, _stream()), name)
         return y
 
-    def apply_profiled(self, which: str, x, y):
+    def apply_profiled(self, which: str, x, y, precision=None):
         """Per-launch-group times (ms) of one apply, in launch order (fio_apply_profiled)."""
         k = {"K": 0, "Kadj": 1, "G": 2, "inv": 3}[which]
         dt, prec, b, ld = _vec(x, self.N)
+        if precision is not None:
+            prec = precision
         cap = 4096
         ms = (ctypes.c_float * cap)()
         nm = ctypes.c_int()
@@ -172,8 +176,10 @@ class Operator:
     def apply_G(self, x, y=None):
         return self._apply(self._lib.fio_apply_G, "fio_apply_G", x, y)
 
-    def apply_inv(self, u, f=None):
-        return self._apply(self._lib.fio_apply_inv, "fio_apply_inv", u, f)
+    def apply_inv(self, u, f=None, precision=None):
+        """f = G-dot K-dot* u; precision defaults to the dtype's (P64 / P32), or FIO_PTF32 /
+        FIO_PBF16 for the tensor-core stage products on complex64 vectors."""
+        return self._apply(self._lib.fio_apply_inv, "fio_apply_inv", u, f, precision)
 
     def apply_inv_host(self, u: np.ndarray, f: np.ndarray | None = None) -> np.ndarray:
         """Host-buffer direct solve: numpy (N, b) Fortran-ordered complex128/complex64 arrays."""

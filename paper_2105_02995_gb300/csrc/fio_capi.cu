@@ -12,6 +12,7 @@
 #include "fio.h"
 #include "fio_internal.h"
 #include "fio_kernels.cuh"
+#include "fio_tc.cuh"
 
 using namespace fio;
 
@@ -62,7 +63,7 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
                                   fio_op* out) {
   if (!packed || !out) return FIO_EINVAL;
   *out = nullptr;
-  if (mask == 0) mask = FIO_MASK_P64 | FIO_MASK_P32;
+  if (mask == 0) mask = FIO_MASK_P64 | FIO_MASK_P32 | FIO_MASK_TC;
   const uint8_t* p = (const uint8_t*)packed;
   if (nbytes < kHeader || memcmp(p, "FIOPACK1", 8) != 0) return FIO_EBADFACTORS;
   const uint32_t version = rd<uint32_t>(p, 8), d = rd<uint32_t>(p, 12);
@@ -144,7 +145,7 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
 
   // per block: extent of the valid rows / columns; CTA tile lists (64-row tiles) per direction
   std::vector<int2> meta;
-  std::vector<size_t> mdims(nst), mfwd(nst), madj(nst);
+  std::vector<size_t> mdims(nst), mfwd(nst), madj(nst), m128f(nst), m128a(nst);
   for (uint64_t si = 0; si < nst; ++si) {
     fio::Stage& st = op->st[si];
     const int32_t* ii = (const int32_t*)(p + st.offIn);
@@ -166,6 +167,14 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
     for (uint32_t b = 0; b < st.nblk; ++b)
       for (int t = 0; t * kTileRows < meta[mdims[si] + b].y; ++t) meta.push_back(make_int2((int)b, t));
     st.ntiles_adj = (int)(meta.size() - madj[si]);
+    m128f[si] = meta.size();
+    for (uint32_t b = 0; b < st.nblk; ++b)
+      for (int t = 0; t * kTcRows < meta[mdims[si] + b].x; ++t) meta.push_back(make_int2((int)b, t));
+    st.n128_fwd = (int)(meta.size() - m128f[si]);
+    m128a[si] = meta.size();
+    for (uint32_t b = 0; b < st.nblk; ++b)
+      for (int t = 0; t * kTcRows < meta[mdims[si] + b].y; ++t) meta.push_back(make_int2((int)b, t));
+    st.n128_adj = (int)(meta.size() - m128a[si]);
   }
 
   cudaStream_t s = (cudaStream_t)stream;
@@ -184,6 +193,8 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
       op->st[si].dims = (const int2*)op->meta + mdims[si];
       op->st[si].tiles_fwd = (const int2*)op->meta + mfwd[si];
       op->st[si].tiles_adj = (const int2*)op->meta + madj[si];
+      op->st[si].t128_fwd = (const int2*)op->meta + m128f[si];
+      op->st[si].t128_adj = (const int2*)op->meta + m128a[si];
     }
   }
   if (cudaMalloc(&op->arena, nbytes) != cudaSuccess) {
@@ -220,8 +231,41 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
       off32 += ne;
     }
   }
-  if (!(mask & FIO_MASK_P64)) {
-    // keep the FP64 copy anyway: the index lists live in the same arena
+  if ((mask & FIO_MASK_TC) && op->arena32) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t tot = 0;
+    for (auto& st : op->st) {
+      const size_t ne = (size_t)st.nblk * st.R * st.C;
+      const int ldbf = (int)((st.C + 3) & ~3u), ldbft = (int)((st.R + 3) & ~3u);
+      tot += al(ne * sizeof(float2)) + al((size_t)st.nblk * st.R * ldbf * 4) + al((size_t)st.nblk * st.C * ldbft * 4);
+    }
+    if (cudaMalloc(&op->arena_tc, tot + 256) != cudaSuccess) {
+      cudaGetLastError();
+      fio_release(op);
+      return FIO_ENOMEM;
+    }
+    op->arena_tc_bytes = tot + 256;
+    uint8_t* q = (uint8_t*)op->arena_tc;
+    for (auto& st : op->st) {
+      const size_t ne = (size_t)st.nblk * st.R * st.C;
+      st.ldbf = (int)((st.C + 3) & ~3u);
+      st.ldbft = (int)((st.R + 3) & ~3u);
+      float2* t32 = (float2*)q;
+      q += al(ne * sizeof(float2));
+      __nv_bfloat162* bf = (__nv_bfloat162*)q;
+      q += al((size_t)st.nblk * st.R * st.ldbf * 4);
+      __nv_bfloat162* bft = (__nv_bfloat162*)q;
+      q += al((size_t)st.nblk * st.C * st.ldbft * 4);
+      st.M32t = t32;
+      st.Mbf = bf;
+      st.Mbft = bft;
+      if (!ne) continue;
+      const unsigned g = (unsigned)((ne + 255) / 256);
+      k_transpose_blocks<<<g, 256, 0, s>>>(st.M32, t32, (int)st.nblk, (int)st.R, (int)st.C);
+      const size_t n1 = (size_t)st.nblk * st.R * st.ldbf, n2 = (size_t)st.nblk * st.C * st.ldbft;
+      k_to_bf16<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(st.M32, bf, (int)st.nblk, (int)st.R, (int)st.C, st.ldbf);
+      k_to_bf16<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(t32, bft, (int)st.nblk, (int)st.C, (int)st.R, st.ldbft);
+    }
   }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
     fio_release(op);
@@ -237,6 +281,7 @@ extern "C" int fio_release(fio_op op) {
   if (op->arena) cudaFree(op->arena);
   if (op->arena32) cudaFree(op->arena32);
   if (op->meta) cudaFree(op->meta);
+  if (op->arena_tc) cudaFree(op->arena_tc);
   if (op->scratch) cudaFree(op->scratch);
   fio_solver_free(op);
   cudaGetLastError();
@@ -250,7 +295,8 @@ extern "C" int fio_query(fio_op op, int* d, int64_t* n, int64_t* N, size_t* devi
   if (n) *n = op->n;
   if (N) *N = op->N;
   if (device_bytes)
-    *device_bytes = op->arena_bytes + op->arena32_bytes + op->meta_bytes + op->scratch_bytes + op->solver_bytes;
+    *device_bytes = op->arena_bytes + op->arena32_bytes + op->arena_tc_bytes + op->meta_bytes +
+                    op->scratch_bytes + op->solver_bytes;
   return FIO_OK;
 }
 
@@ -383,10 +429,76 @@ void launch_stage_dir(const StageArgs<V>& a, cudaStream_t s) {
   }
 }
 
+// stage arithmetic of the float2 path: 0 FP32 CUDA cores, 1 TF32 / 2 BF16 tensor cores (tcgen05);
+// set for the duration of one public call (TcMode), read by launch_stage
+thread_local int g_tc_mode = 0;
+struct TcMode {
+  int prev;
+  explicit TcMode(int m) : prev(g_tc_mode) { g_tc_mode = m; }
+  ~TcMode() { g_tc_mode = prev; }
+};
+inline int tc_mode_of(int prec) { return prec == FIO_PTF32 ? 1 : (prec == FIO_PBF16 ? 2 : 0); }
+
+template <bool ADJ, bool BF16>
+void launch_tc_dir(const TcArgs& a, int ncta, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_stage_tc<ADJ, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes());
+    attr = true;
+  }
+  dim3 grid((unsigned)ncta, (unsigned)((a.b + kTcMaxRhs - 1) / kTcMaxRhs));
+  k_stage_tc<ADJ, BF16><<<grid, 128, tc_smem_bytes(), s>>>(a);
+}
+
+void launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long long xcs, float2* y,
+               long long yrs, long long ycs, int b, cudaStream_t s) {
+  const bool bf = g_tc_mode == 2;
+  TcArgs a;
+  if (!adj) {
+    a.A = bf ? (const void*)st.Mbf : (const void*)st.M32;
+    a.lda = bf ? st.ldbf : (int)st.C;
+    a.bstride = (long long)st.R * a.lda;
+  } else {
+    a.A = bf ? (const void*)st.Mbft : (const void*)st.M32t;
+    a.lda = bf ? st.ldbft : (int)st.R;
+    a.bstride = (long long)st.C * a.lda;
+  }
+  a.rowidx = adj ? st.in : st.out;
+  a.colidx = adj ? st.out : st.in;
+  a.ldr = (int)st.R;
+  a.ldc = (int)st.C;
+  a.dims = st.dims;
+  a.tiles = adj ? st.t128_adj : st.t128_fwd;
+  const int ncta = adj ? st.n128_adj : st.n128_fwd;
+  a.x = x;
+  a.xrs = xrs;
+  a.xcs = xcs;
+  a.y = y;
+  a.yrs = yrs;
+  a.ycs = ycs;
+  a.b = b;
+  if (ncta == 0) return;
+  if (adj) bf ? launch_tc_dir<true, true>(a, ncta, s) : launch_tc_dir<true, false>(a, ncta, s);
+  else bf ? launch_tc_dir<false, true>(a, ncta, s) : launch_tc_dir<false, false>(a, ncta, s);
+}
+
+template <typename V>
+bool use_tc(const Stage& st, int b) {
+  return false;
+}
+template <>
+bool use_tc<float2>(const Stage& st, int b) {
+  return g_tc_mode != 0 && b >= 8 && st.M32t != nullptr;
+}
+
 template <typename V>
 void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long long xcs, V* y,
                   long long yrs, long long ycs, int b, cudaStream_t s) {
   if (st.nblk == 0) return;
+  if (use_tc<V>(st, b)) {
+    launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s);
+    return;
+  }
   StageArgs<V> a;
   a.M = stage_M<V>(st);
   a.in = st.in;
@@ -473,8 +585,10 @@ int check_args(fio_op op, const void* x, const void* y, int64_t ld, int b, int d
   if (!op || b < 0) return FIO_EINVAL;
   if (b > 0 && (!x || !y || x == y)) return FIO_EINVAL;
   if (ld < op->N) return FIO_EINVAL;
-  if (!((dtype == FIO_C128 && prec == FIO_P64) || (dtype == FIO_C64 && prec == FIO_P32))) return FIO_EINVAL;
-  if (prec == FIO_P32 && !op->arena32) return FIO_EINVAL;
+  const bool c64prec = prec == FIO_P32 || prec == FIO_PTF32 || prec == FIO_PBF16;
+  if (!((dtype == FIO_C128 && prec == FIO_P64) || (dtype == FIO_C64 && c64prec))) return FIO_EINVAL;
+  if (c64prec && !op->arena32) return FIO_EINVAL;
+  if ((prec == FIO_PTF32 || prec == FIO_PBF16) && !op->arena_tc) return FIO_EINVAL;
   const size_t es = dtype == FIO_C128 ? 16 : 8;
   const uint8_t *xb = (const uint8_t*)x, *yb = (const uint8_t*)y;
   const size_t span = ((size_t)ld * (b > 0 ? b - 1 : 0) + op->N) * es;
@@ -519,8 +633,9 @@ int apply_any(fio_op op, Which w, const void* x, void* y, int64_t ld, int b, int
   if (b == 0) return FIO_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaGetLastError() != cudaSuccess) return FIO_ECUDA;
-  return prec == FIO_P64 ? apply_t<double2>(op, w, x, y, ld, b, s)
-                         : apply_t<float2>(op, w, x, y, ld, b, s);
+  if (prec == FIO_P64) return apply_t<double2>(op, w, x, y, ld, b, s);
+  TcMode m(tc_mode_of(prec));
+  return apply_t<float2>(op, w, x, y, ld, b, s);
 }
 
 }  // namespace
@@ -529,8 +644,16 @@ int apply_any(fio_op op, Which w, const void* x, void* y, int64_t ld, int b, int
 int fio_apply_internal(fio_op op, int which, const void* x, void* y, int64_t ld, int b, int prec,
                        cudaStream_t s) {
   if (b == 0) return FIO_OK;
-  return prec == FIO_P64 ? apply_t<double2>(op, (Which)which, x, y, ld, b, s)
-                         : apply_t<float2>(op, (Which)which, x, y, ld, b, s);
+  if (prec == FIO_P64) return apply_t<double2>(op, (Which)which, x, y, ld, b, s);
+  TcMode m(tc_mode_of(prec));
+  return apply_t<float2>(op, (Which)which, x, y, ld, b, s);
+}
+
+int fio_tc_timeout_reset() {
+  int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_timeout, sizeof(int)) != cudaSuccess) return -1;
+  if (v) cudaMemcpyToSymbol(g_tc_timeout, &zero, sizeof(int));
+  return v;
 }
 
 extern "C" int fio_apply_K(fio_op op, const void* x, void* y, int64_t ld, int b, int dtype,
@@ -553,8 +676,10 @@ extern "C" int fio_apply_inv(fio_op op, const void* u, void* f, int64_t ld, int 
 extern "C" int fio_apply_inv_host(fio_op op, const void* u_host, void* f_host, int64_t ld, int b,
                                   int dtype, int precision, void* stream) {
   if (!op || !u_host || !f_host || b < 0 || ld < op->N) return FIO_EINVAL;
-  if (!((dtype == FIO_C128 && precision == FIO_P64) || (dtype == FIO_C64 && precision == FIO_P32)))
+  if (!((dtype == FIO_C128 && precision == FIO_P64) ||
+        (dtype == FIO_C64 && (precision == FIO_P32 || precision == FIO_PTF32 || precision == FIO_PBF16))))
     return FIO_EINVAL;
+  if ((precision == FIO_PTF32 || precision == FIO_PBF16) && !op->arena_tc) return FIO_EINVAL;
   if (op->n_root == 0) return FIO_ENOTSUP;
   if (b == 0) return FIO_OK;
   cudaStream_t s = (cudaStream_t)stream;
@@ -606,14 +731,18 @@ extern "C" int fio_apply_profiled(fio_op op, int which, const void* x, void* y, 
   Marks m{ev.data() + 1, cap, 0};
   cudaEventRecord(ev[0], s);
   g_marks = &m;
-  rc = precision == FIO_P64 ? apply_t<double2>(op, (Which)which, x, y, ld, b, s)
-                            : apply_t<float2>(op, (Which)which, x, y, ld, b, s);
+  {
+    TcMode mode(tc_mode_of(precision));
+    rc = precision == FIO_P64 ? apply_t<double2>(op, (Which)which, x, y, ld, b, s)
+                              : apply_t<float2>(op, (Which)which, x, y, ld, b, s);
+  }
   g_marks = nullptr;
   if (rc == FIO_OK) {
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = FIO_ECUDA;
     for (int k = 0; rc == FIO_OK && k < m.n; ++k)
       if (cudaEventElapsedTime(&stage_ms[k], ev[k], ev[k + 1]) != cudaSuccess) rc = FIO_ECUDA;
     *nmarks = m.n;
+    if (rc == FIO_OK && fio_tc_timeout_reset() > 0) rc = FIO_ETIMEOUT;
   }
   for (auto& e : ev) cudaEventDestroy(e);
   return rc;

@@ -1,6 +1,7 @@
 // fio_internal.h -- operator object shared by the translation units of libfio (not installed).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,6 +27,15 @@ struct Stage {
   const int2* tiles_fwd = nullptr;  // device, (block, tile) pairs
   const int2* tiles_adj = nullptr;
   int ntiles_fwd = 0, ntiles_adj = 0;
+  // tensor-core copies (FIO_MASK_TC): block-transposed complex64 (C x R per block), bf16 in both
+  // orientations with row strides padded to a multiple of 4; 128-row tile lists
+  const float2* M32t = nullptr;
+  const __nv_bfloat162* Mbf = nullptr;
+  const __nv_bfloat162* Mbft = nullptr;
+  int ldbf = 0, ldbft = 0;
+  const int2* t128_fwd = nullptr;
+  const int2* t128_adj = nullptr;
+  int n128_fwd = 0, n128_adj = 0;
 };
 
 }  // namespace fio
@@ -43,6 +53,8 @@ struct fio_op_s {
   size_t arena32_bytes = 0;
   void* scratch = nullptr;        // 5 work arrays of max_len x b (grown on demand)
   size_t scratch_bytes = 0;
+  void* arena_tc = nullptr;       // tensor-core copies of every stage's blocks
+  size_t arena_tc_bytes = 0;
   void* meta = nullptr;           // per-block dims and tile lists of every stage
   size_t meta_bytes = 0;
   void* solver = nullptr;         // solver work arrays (fio_solve.cu)
@@ -55,3 +67,6 @@ int fio_scratch(fio_op op, int b, size_t elem, cudaStream_t s, void** bufs);
 int fio_apply_internal(fio_op op, int which, const void* x, void* y, int64_t ld, int b, int prec,
                        cudaStream_t s);
 void fio_solver_free(fio_op op);
+// 1 when a tensor-core kernel's bounded wait gave up since the last call (and clear the flag),
+// 0 otherwise, -1 on a CUDA error
+int fio_tc_timeout_reset();

@@ -241,8 +241,9 @@ extern "C" int fio_solve(fio_op op, const void* uv, void* fv, int64_t ld, int b,
   if (!op || !opts || b < 0 || dtype != FIO_C128 || ld != op->N) return FIO_EINVAL;
   if (b > 0 && (!uv || !fv || uv == fv)) return FIO_EINVAL;
   if (opts->method < FIO_DIRECT || opts->method > FIO_IR) return FIO_EINVAL;
-  if (opts->inner != FIO_P64 && opts->inner != FIO_P32) return FIO_EINVAL;
-  if (opts->inner == FIO_P32 && !op->arena32) return FIO_EINVAL;
+  if (opts->inner < FIO_P64 || opts->inner > FIO_PBF16) return FIO_EINVAL;
+  if (opts->inner != FIO_P64 && !op->arena32) return FIO_EINVAL;
+  if ((opts->inner == FIO_PTF32 || opts->inner == FIO_PBF16) && !op->arena_tc) return FIO_EINVAL;
   if (op->n_root == 0) return FIO_ENOTSUP;
   if (b == 0) return FIO_OK;
   const int maxit = opts->maxit > 0 ? opts->maxit : 100;
@@ -491,6 +492,7 @@ extern "C" int fio_solve(fio_op op, const void* uv, void* fv, int64_t ld, int b,
     }
   }
   if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return FIO_ECUDA;
+  if (fio_tc_timeout_reset() > 0) return FIO_ETIMEOUT;
   bool conv = true;
   for (int j = 0; j < b; ++j) {
     const bool ok = relres[j] <= tol || opts->method == FIO_DIRECT;

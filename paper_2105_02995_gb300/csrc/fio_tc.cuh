@@ -1,0 +1,292 @@
+// fio_tc.cuh -- tcgen05 tensor-core stage kernel (sm_103a) for batched right-hand sides.
+//
+// One stage block product y = op(M) x with complex M (rows x cols) and b right-hand sides is the
+// real GEMM
+//     [y_re y_im]-interleaved (rows x 2b)  =  A (rows x 2 cols)  *  B (2 cols x 2b)
+// where A is the block's complex row data read as interleaved reals (re, im, re, im, ...) -- the
+// stored factor itself, already "K-major" -- and B is built from the gathered x rows:
+//     forward  (y = M x):   B[2c][2j] = xr,  B[2c+1][2j] = -xi,  B[2c][2j+1] = xi, B[2c+1][2j+1] = xr
+//     adjoint  (y = M^H x, A = the block-transposed copy M^T):
+//                           B[2c][2j] = xr,  B[2c+1][2j] =  xi,  B[2c][2j+1] = xi, B[2c+1][2j+1] = -xr
+// so the (re, im) pair of output (r, j) lands in accumulator columns 2j, 2j+1 of row r.
+//
+// CTA = 128 threads, one 128-row tile of one block and up to 64 right-hand sides: accumulator
+// D[128 x 2bp] fp32 in tensor memory (TMEM), operands in shared memory in the canonical K-major
+// layout with 128-byte swizzle (8-row x 128-byte atoms, 1024 bytes apart).  Per chunk of the
+// block's columns (128 bytes of K per row: 16 complex in TF32, 32 complex in BF16): the A tile
+// arrives by 16-byte cp.async, the B tile is written by the threads, one elected thread issues
+// four tcgen05.mma (K = 8 TF32 / 16 BF16 each) and commits them to an mbarrier that every
+// thread waits on (bounded by %globaltimer: after kWaitNs the kernel records a timeout and
+// stops issuing).  Tensor memory is allocated by warp 0 and freed on every path.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fio {
+
+__device__ int g_tc_timeout;  // set when a bounded wait in k_stage_tc gave up
+
+namespace tc {
+
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(n) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try(bar, parity))
+    if (globaltimer() - t0 > kWaitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// shared memory descriptor: K-major, 128-byte swizzle, atoms of 8 rows x 128 bytes 1024 bytes apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused: K of one MMA < 128 B)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+// instruction descriptor: D fp32, A/B format (2 = TF32 under kind::tf32, 1 = BF16 under kind::f16),
+// both K-major, N and M
+__host__ __device__ constexpr uint32_t idesc(uint32_t ab_fmt, int M, int N) {
+  return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if (BF16)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// byte offset of (row, 16-byte chunk) in a K-major 128-byte-swizzled tile
+__device__ __forceinline__ uint32_t swz(int row, int chunk) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+}  // namespace tc
+
+struct TcArgs {
+  const void* A;      // op-matrix blocks: float2 (TF32) or __nv_bfloat162 (BF16), row-major
+  long long bstride;  // elements between blocks
+  int lda;            // elements between rows
+  const int* rowidx;  // output index list base (out for forward, in for adjoint), per block stride
+  const int* colidx;  // input index list base
+  int ldr, ldc;       // index-list strides per block (R or C of the packed stage)
+  const int2* dims;   // per block (valid rows, valid cols) of the forward block
+  const int2* tiles;  // per CTA (block, 128-row tile)
+  const float2* x;
+  long long xrs, xcs;
+  float2* y;
+  long long yrs, ycs;
+  int b;
+};
+
+constexpr int kTcRows = 128;
+constexpr int kTcMaxRhs = 64;  // right-hand sides per CTA (N = 128 accumulator columns)
+
+__host__ __device__ constexpr int tc_smem_bytes() { return 16384 + 2 * kTcMaxRhs * 128 + 1024; }
+
+template <bool ADJ, bool BF16>
+__global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
+  using namespace tc;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  extern __shared__ __align__(16) uint8_t smem_dyn[];
+  // 1024-byte aligned tiles (swizzle atoms must start on 1024-byte boundaries)
+  const uint32_t base = (su32(smem_dyn) + 1023u) & ~1023u;
+  uint8_t* gbase = smem_dyn + (base - su32(smem_dyn));
+  const uint32_t sA = base, sB = base + 16384;
+  uint8_t* pB = gbase + 16384;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int2 t = a.tiles[blockIdx.x];
+  const int blk = t.x, r0 = t.y * kTcRows;
+  const int2 d = a.dims[blk];
+  const int nrows = ADJ ? d.y : d.x, ncols = ADJ ? d.x : d.y;
+  const int j0 = blockIdx.y * kTcMaxRhs;
+  const int bcta = min(kTcMaxRhs, a.b - j0);
+  const int bp = (bcta + 7) & ~7;  // right-hand sides padded to 8: N = 2 bp, a multiple of 16
+  const int N = 2 * bp;
+  const uint32_t ncol_tmem = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+  const int* rowidx = a.rowidx + (size_t)blk * (ADJ ? a.ldc : a.ldr);
+  const int* colidx = a.colidx + (size_t)blk * (ADJ ? a.ldr : a.ldc);
+  constexpr int ESZ = BF16 ? 4 : 8;        // bytes per complex entry of A
+  constexpr int KC = 128 / ESZ;            // complex columns per 128-byte chunk
+  constexpr int CPC = 16 / ESZ;            // complex entries per 16-byte copy
+  const uint8_t* Ab = (const uint8_t*)a.A + (size_t)blk * a.bstride * ESZ;
+  const uint32_t id = idesc(BF16 ? 1u : 2u, kTcRows, N);
+
+  if (warp == 0) tmem_alloc(&s_tmem, ncol_tmem);
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s_tmem;
+
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int c0 = 0; c0 < ncols && ok; c0 += KC) {
+    // A tile: 128 rows x 128 bytes, 16-byte cp.async with zero fill outside the block
+    for (int e = tid; e < kTcRows * 8; e += 128) {
+      const int row = e >> 3, ch = e & 7;
+      const int gr = r0 + row, gc = c0 + ch * CPC;
+      const bool in = gr < nrows && gc < ncols;
+      const void* src = in ? (const void*)(Ab + ((size_t)gr * a.lda + gc) * ESZ) : a.A;
+      cp16(sA + swz(row, ch), src, in ? 16 : 0);
+    }
+    // B^T tile: rows n = 2j (real part of output j), 2j+1 (imaginary part); K = 2c, 2c+1
+    for (int e = tid; e < KC * bp; e += 128) {
+      const int c = e / bp, j = e - c * bp;
+      float2 v = make_float2(0.f, 0.f);
+      if (c0 + c < ncols && j < bcta) {
+        const int idx = colidx[c0 + c];
+        if (idx >= 0) v = a.x[(long long)idx * a.xrs + (long long)(j0 + j) * a.xcs];
+      }
+      float p0, p1, q0, q1;  // row 2j: (p0, p1), row 2j+1: (q0, q1)
+      if (!ADJ) {
+        p0 = v.x; p1 = -v.y; q0 = v.y; q1 = v.x;
+      } else {
+        p0 = v.x; p1 = v.y; q0 = v.y; q1 = -v.x;
+      }
+      const int n0 = 2 * j, n1 = 2 * j + 1;
+      if (BF16) {
+        const int ch = c >> 2, off = (c & 3) << 2;
+        *reinterpret_cast<__nv_bfloat162*>(pB + swz(n0, ch) + off) = __floats2bfloat162_rn(p0, p1);
+        *reinterpret_cast<__nv_bfloat162*>(pB + swz(n1, ch) + off) = __floats2bfloat162_rn(q0, q1);
+      } else {
+        const int ch = c >> 1, off = (c & 1) << 3;
+        *reinterpret_cast<float2*>(pB + swz(n0, ch) + off) = make_float2(p0, p1);
+        *reinterpret_cast<float2*>(pB + swz(n1, ch) + off) = make_float2(q0, q1);
+      }
+    }
+    cp_wait_all();
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after();
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        mma<BF16>(tmem, sdesc(sA + 32 * k), sdesc(sB + 32 * k), id, (c0 > 0 || k > 0) ? 1u : 0u);
+      mma_commit(&s_bar);
+    }
+    // every thread waits for the MMAs that read the tiles it overwrites next; a timeout anywhere
+    // stops the whole CTA (the result must be CTA-uniform: TMEM loads are warp-collective)
+    ok = __syncthreads_and(mbar_wait(&s_bar, phase) ? 1 : 0) != 0;
+    phase ^= 1;
+    fence_after();
+  }
+  if (!ok) atomicExch(&g_tc_timeout, 1);
+
+  // epilogue: warp w holds accumulator rows 32w .. 32w+31 (TMEM lanes)
+  const int row = r0 + warp * 32 + lane;
+  const int oidx = (row < nrows) ? rowidx[row] : -1;
+  for (int cb = 0; cb < N; cb += 16) {
+    uint32_t r[16];
+    if (ncols > 0 && ok) {
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, r);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) r[q] = 0u;
+    }
+    if (oidx >= 0) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = cb / 2 + q;
+        if (j < bcta)
+          a.y[(long long)oidx * a.yrs + (long long)(j0 + j) * a.ycs] =
+              make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncol_tmem);
+}
+
+// block-wise transpose of the complex64 copy: out block (C x R) = in block (R x C)^T
+__global__ void k_transpose_blocks(const float2* in, float2* out, int nblk, int R, int C) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)R * C;
+  if (t >= per * nblk) return;
+  const long long b = t / per, e = t - b * per;
+  const int r = (int)(e / C), c = (int)(e - (long long)r * C);
+  out[b * per + (long long)c * R + r] = in[t];
+}
+
+// bf16 copy with row stride ld (>= cols, padding zero): out[b][r][0..ld) from in[b][r][0..cols)
+__global__ void k_to_bf16(const float2* in, __nv_bfloat162* out, int nblk, int rows, int cols, int ld) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)rows * ld;
+  if (t >= per * nblk) return;
+  const long long b = t / per, e = t - b * per;
+  const int r = (int)(e / ld), c = (int)(e - (long long)r * ld);
+  const float2 v = c < cols ? in[b * (long long)rows * cols + (long long)r * cols + c] : make_float2(0.f, 0.f);
+  out[t] = __floats2bfloat162_rn(v.x, v.y);
+}
+
+}  // namespace fio

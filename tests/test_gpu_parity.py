@@ -147,3 +147,46 @@ def test_iterative_solves(method, inner):
         assert it <= 12  # the paper: 2-3 PCG iterations at eps = 1e-6
     f_ex = np.linalg.solve(Kd, u)
     assert rel(fh, f_ex) < 1e-8
+
+
+# Tensor-core precisions (tcgen05): operands rounded to TF32 (unit roundoff 2^-11) or bfloat16
+# (2^-8) before products accumulated in FP32.  Per stage ~sqrt(2) u relative, over up to ~15
+# stages in a row: TF32 ~ 3e-3, BF16 ~ 2e-2; the bounds below leave a factor ~3.
+TOL_TC = {binding.FIO_PTF32: 1e-2, binding.FIO_PBF16: 5e-2}
+
+
+@pytest.mark.parametrize("name", ["ex1_256", "ex3_32"])
+@pytest.mark.parametrize("prec", [binding.FIO_PTF32, binding.FIO_PBF16])
+@pytest.mark.parametrize("b", [8, 32, 40, 72])
+def test_apply_tensor_core_vs_factor_oracle(name, prec, b):
+    import ctypes
+    buf, info, P, op, ofo = get(name)
+    lib = binding.load()
+    x = complex_gaussian(ofo.N, b, rhs_seed(0, 300 + b))
+    xd = dev(x, torch.complex64)
+    x64 = x.astype(np.complex64).astype(np.complex128)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for what, fn, ref in (("K", lib.fio_apply_K, fa.apply_Kdot), ("Kadj", lib.fio_apply_Kadj, fa.apply_Kdot_adj),
+                          ("inv", lib.fio_apply_inv, fa.apply_inv)):
+        y = binding.colmajor(torch.empty_like(xd))
+        rc = fn(op.h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(y.data_ptr()), ofo.N, b,
+                binding.FIO_C64, prec, stream)
+        assert rc == 0, (what, rc)
+        torch.cuda.synchronize()
+        err = rel(host(y), ref(P, x64))
+        assert err < TOL_TC[prec], (what, err)
+
+
+@pytest.mark.parametrize("prec", [binding.FIO_PTF32, binding.FIO_PBF16])
+def test_refinement_with_tensor_core_inner(prec):
+    """FP64 iterative refinement whose correction G-dot K-dot* r runs on the tensor cores still
+    reaches 1e-10 (the outer FP64 residual removes the inner rounding)."""
+    buf, info, P, op, ofo = get("ex1_256")
+    u = complex_gaussian(ofo.N, 8, rhs_seed(2))
+    f, infos = op.solve(dev(u), method=binding.FIO_IR, inner=prec, tol=1e-10, maxit=60)
+    torch.cuda.synchronize()
+    Kd = fa.dense_Kdot(P)
+    fh = host(f)
+    for j, (it, rr, st) in enumerate(infos):
+        assert st == 0 and rr <= 1e-10, infos
+        assert np.linalg.norm(u[:, j] - Kd @ fh[:, j]) / np.linalg.norm(u[:, j]) < 3e-10
