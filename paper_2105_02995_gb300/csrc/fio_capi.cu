@@ -3,8 +3,11 @@
 // operator bookkeeping.  The iterative solvers live in fio_solve.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -441,13 +444,15 @@ inline int tc_mode_of(int prec) { return prec == FIO_PTF32 ? 1 : (prec == FIO_PB
 
 template <bool ADJ, bool BF16>
 void launch_tc_dir(const TcArgs& a, int ncta, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_stage_tc<ADJ, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes());
-    attr = true;
+  static int cap = 48 * 1024;  // dynamic shared memory allowed without opting in
+  const int need = tc_smem_bytes(BF16, a.nmax, a.ncmax);
+  if (need > cap) {
+    if (cudaFuncSetAttribute(k_stage_tc<ADJ, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, need) ==
+        cudaSuccess)
+      cap = need;
   }
   dim3 grid((unsigned)ncta, (unsigned)((a.b + kTcMaxRhs - 1) / kTcMaxRhs));
-  k_stage_tc<ADJ, BF16><<<grid, 128, tc_smem_bytes(), s>>>(a);
+  k_stage_tc<ADJ, BF16><<<grid, 128, tc_smem_bytes(BF16, a.nmax, a.ncmax), s>>>(a);
 }
 
 void launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long long xcs, float2* y,
@@ -477,6 +482,9 @@ void launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long l
   a.yrs = yrs;
   a.ycs = ycs;
   a.b = b;
+  a.nmax = 2 * ((std::min(b, kTcMaxRhs) + 7) & ~7);
+  a.stage_x = (xcs == 1 && xrs % 2 == 0 && b % 2 == 0 && ((uintptr_t)x & 15) == 0) ? 1 : 0;
+  a.ncmax = adj ? (int)st.R : (int)st.C;  // gather list length per block (forward: in, adjoint: out)
   if (ncta == 0) return;
   if (adj) bf ? launch_tc_dir<true, true>(a, ncta, s) : launch_tc_dir<true, false>(a, ncta, s);
   else bf ? launch_tc_dir<false, true>(a, ncta, s) : launch_tc_dir<false, false>(a, ncta, s);
@@ -596,7 +604,12 @@ int check_args(fio_op op, const void* x, const void* y, int64_t ld, int b, int d
   return FIO_OK;
 }
 
-int finish(cudaStream_t) { return cudaGetLastError() == cudaSuccess ? FIO_OK : FIO_ECUDA; }
+int finish(cudaStream_t) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return FIO_OK;
+  if (getenv("FIO_DEBUG")) fprintf(stderr, "libfio: %s\n", cudaGetErrorString(e));
+  return FIO_ECUDA;
+}
 
 enum Which { W_K = 0, W_KADJ = 1, W_G = 2, W_INV = 3 };
 
@@ -738,7 +751,11 @@ extern "C" int fio_apply_profiled(fio_op op, int which, const void* x, void* y, 
   }
   g_marks = nullptr;
   if (rc == FIO_OK) {
-    if (cudaStreamSynchronize(s) != cudaSuccess) rc = FIO_ECUDA;
+    const cudaError_t se = cudaStreamSynchronize(s);
+    if (se != cudaSuccess) {
+      if (getenv("FIO_DEBUG")) fprintf(stderr, "libfio: %s\n", cudaGetErrorString(se));
+      rc = FIO_ECUDA;
+    }
     for (int k = 0; rc == FIO_OK && k < m.n; ++k)
       if (cudaEventElapsedTime(&stage_ms[k], ev[k], ev[k + 1]) != cudaSuccess) rc = FIO_ECUDA;
     *nmarks = m.n;

@@ -12,12 +12,15 @@
 //
 // CTA = 128 threads, one 128-row tile of one block and up to 64 right-hand sides: accumulator
 // D[128 x 2bp] fp32 in tensor memory (TMEM), operands in shared memory in the canonical K-major
-// layout with 128-byte swizzle (8-row x 128-byte atoms, 1024 bytes apart).  Per chunk of the
-// block's columns (128 bytes of K per row: 16 complex in TF32, 32 complex in BF16): the A tile
-// arrives by 16-byte cp.async, the B tile is written by the threads, one elected thread issues
-// four tcgen05.mma (K = 8 TF32 / 16 BF16 each) and commits them to an mbarrier that every
-// thread waits on (bounded by %globaltimer: after kWaitNs the kernel records a timeout and
-// stops issuing).  Tensor memory is allocated by warp 0 and freed on every path.
+// layout with 128-byte swizzle (8-row x 128-byte atoms, 1024 bytes apart).  The block's columns
+// are consumed in chunks of 128 bytes of K per row (16 complex in TF32, 32 in BF16): the A tile
+// and the chunk's gathered x rows arrive by 16-byte cp.async, the threads expand the x rows into
+// the B tile, one elected thread issues four tcgen05.mma (K = 8 TF32 / 16 BF16 each) and commits
+// them to an mbarrier; the tiles are refilled once that phase completes (waits bounded by
+// %globaltimer: after kWaitNs the kernel records a timeout and stops issuing).  One operand buffer
+// per CTA keeps shared memory near 30 KB so that six to seven CTAs share an SM and overlap one
+// another's copies and MMAs; measured faster than two or three buffers per CTA at fewer CTAs.
+// Tensor memory is allocated by warp 0 and freed on every path.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -140,12 +143,19 @@ struct TcArgs {
   float2* y;
   long long yrs, ycs;
   int b;
+  int nmax;           // accumulator width N of a full right-hand-side tile (sets the smem layout)
+  int stage_x;        // x rows are 16-byte aligned and contiguous: gather them with cp.async
+  int ncmax;          // longest gather list of a block (sizes the shared copy of the list)
 };
 
 constexpr int kTcRows = 128;
 constexpr int kTcMaxRhs = 64;  // right-hand sides per CTA (N = 128 accumulator columns)
-
-__host__ __device__ constexpr int tc_smem_bytes() { return 16384 + 2 * kTcMaxRhs * 128 + 1024; }
+// dynamic shared memory: A tile (16 KB) + B tile (N x 128 B) + staging of the chunk's x rows
+// (KC rows x N/2 complex) + alignment slack, for accumulator width N (= 2 x right-hand sides)
+// + the block's gather list (ncmax int32)
+__host__ __device__ constexpr int tc_smem_bytes(bool bf16, int N, int ncmax) {
+  return 16384 + N * 128 + (bf16 ? 32 : 16) * (N / 2) * 8 + 1024 + ((ncmax + 3) & ~3) * 4;
+}
 
 template <bool ADJ, bool BF16>
 __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
@@ -153,11 +163,15 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
   extern __shared__ __align__(16) uint8_t smem_dyn[];
-  // 1024-byte aligned tiles (swizzle atoms must start on 1024-byte boundaries)
+  // layout: A tile (16 KB, 1024-byte aligned for the swizzle atoms), B tile (N x 128 B), x staging
+  // (KC rows x nmax/2 complex)
   const uint32_t base = (su32(smem_dyn) + 1023u) & ~1023u;
   uint8_t* gbase = smem_dyn + (base - su32(smem_dyn));
   const uint32_t sA = base, sB = base + 16384;
   uint8_t* pB = gbase + 16384;
+  const uint32_t sX = sB + (uint32_t)a.nmax * 128;
+  const float2* pX = reinterpret_cast<const float2*>(gbase + 16384 + a.nmax * 128);
+  int* sIdx = reinterpret_cast<int*>(gbase + 16384 + a.nmax * 128 + (BF16 ? 32 : 16) * (a.nmax / 2) * 8);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int2 t = a.tiles[blockIdx.x];
@@ -168,29 +182,39 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
   const int bcta = min(kTcMaxRhs, a.b - j0);
   const int bp = (bcta + 7) & ~7;  // right-hand sides padded to 8: N = 2 bp, a multiple of 16
   const int N = 2 * bp;
+  const int sld = a.nmax / 2;      // staging row length (complex)
   const uint32_t ncol_tmem = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
   const int* rowidx = a.rowidx + (size_t)blk * (ADJ ? a.ldc : a.ldr);
   const int* colidx = a.colidx + (size_t)blk * (ADJ ? a.ldr : a.ldc);
-  constexpr int ESZ = BF16 ? 4 : 8;        // bytes per complex entry of A
-  constexpr int KC = 128 / ESZ;            // complex columns per 128-byte chunk
-  constexpr int CPC = 16 / ESZ;            // complex entries per 16-byte copy
+  constexpr int ESZ = BF16 ? 4 : 8;  // bytes per complex entry of A
+  constexpr int KC = 128 / ESZ;      // complex columns per 128-byte chunk
+  constexpr int CPC = 16 / ESZ;      // complex entries per 16-byte copy
   const uint8_t* Ab = (const uint8_t*)a.A + (size_t)blk * a.bstride * ESZ;
   const uint32_t id = idesc(BF16 ? 1u : 2u, kTcRows, N);
+  const int nchunks = (ncols + KC - 1) / KC;
 
   if (warp == 0) tmem_alloc(&s_tmem, ncol_tmem);
   if (tid == 0) {
     mbar_init(&s_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // the block's gather list, once per CTA: the per-chunk copies then never wait on it
+  for (int e = tid; e < ncols; e += 128) sIdx[e] = colidx[e];
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = s_tmem;
 
-  uint32_t phase = 0;
   bool ok = true;
-  for (int c0 = 0; c0 < ncols && ok; c0 += KC) {
-    // A tile: 128 rows x 128 bytes, 16-byte cp.async with zero fill outside the block
+  for (int k = 0; k < nchunks && ok; ++k) {
+    const int c0 = k * KC;
+    // the previous chunk's MMAs must be done with the tiles before they are overwritten
+    if (k >= 1) {
+      ok = __syncthreads_and(mbar_wait(&s_bar, (uint32_t)((k - 1) & 1)) ? 1 : 0) != 0;
+      fence_after();
+      if (!ok) break;
+    }
+    // A tile: 128 rows x 128 bytes of the block, 16-byte cp.async, zero fill outside the block
     for (int e = tid; e < kTcRows * 8; e += 128) {
       const int row = e >> 3, ch = e & 7;
       const int gr = r0 + row, gc = c0 + ch * CPC;
@@ -198,15 +222,31 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
       const void* src = in ? (const void*)(Ab + ((size_t)gr * a.lda + gc) * ESZ) : a.A;
       cp16(sA + swz(row, ch), src, in ? 16 : 0);
     }
-    // B^T tile: rows n = 2j (real part of output j), 2j+1 (imaginary part); K = 2c, 2c+1
+    if (a.stage_x) {
+      // the chunk's gathered x rows (bcta complex each, contiguous): 16-byte copies into staging
+      const int cpr = bcta >> 1;
+      for (int e = tid; e < KC * cpr; e += 128) {
+        const int c = e / cpr, q = e - c * cpr;
+        const int idx = (c0 + c < ncols) ? sIdx[c0 + c] : -1;
+        const void* src = idx >= 0 ? (const void*)(a.x + (long long)idx * a.xrs + j0 + 2 * q) : (const void*)a.x;
+        cp16(sX + (uint32_t)((c * sld + 2 * q) * 8), src, idx >= 0 ? 16 : 0);
+      }
+    }
+    cp_wait_all();
+    __syncthreads();
+    // B^T tile: rows 2j / 2j+1 = real / imaginary part of output j; K = (2c, 2c+1)
     for (int e = tid; e < KC * bp; e += 128) {
       const int c = e / bp, j = e - c * bp;
       float2 v = make_float2(0.f, 0.f);
-      if (c0 + c < ncols && j < bcta) {
-        const int idx = colidx[c0 + c];
-        if (idx >= 0) v = a.x[(long long)idx * a.xrs + (long long)(j0 + j) * a.xcs];
+      if (j < bcta) {
+        if (a.stage_x) {
+          v = pX[c * sld + j];
+        } else if (c0 + c < ncols) {
+          const int idx = sIdx[c0 + c];
+          if (idx >= 0) v = a.x[(long long)idx * a.xrs + (long long)(j0 + j) * a.xcs];
+        }
       }
-      float p0, p1, q0, q1;  // row 2j: (p0, p1), row 2j+1: (q0, q1)
+      float p0, p1, q0, q1;
       if (!ADJ) {
         p0 = v.x; p1 = -v.y; q0 = v.y; q1 = v.x;
       } else {
@@ -223,31 +263,31 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
         *reinterpret_cast<float2*>(pB + swz(n1, ch) + off) = make_float2(q0, q1);
       }
     }
-    cp_wait_all();
     fence_async_smem();
     fence_before();
     __syncthreads();
     if (tid == 0) {
       fence_after();
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        mma<BF16>(tmem, sdesc(sA + 32 * k), sdesc(sB + 32 * k), id, (c0 > 0 || k > 0) ? 1u : 0u);
+      for (int q = 0; q < 4; ++q)
+        mma<BF16>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
       mma_commit(&s_bar);
     }
-    // every thread waits for the MMAs that read the tiles it overwrites next; a timeout anywhere
-    // stops the whole CTA (the result must be CTA-uniform: TMEM loads are warp-collective)
-    ok = __syncthreads_and(mbar_wait(&s_bar, phase) ? 1 : 0) != 0;
-    phase ^= 1;
+  }
+  // drain: the last commit tracks every MMA issued before it
+  if (nchunks > 0 && ok) {
+    ok = __syncthreads_and(mbar_wait(&s_bar, (uint32_t)((nchunks - 1) & 1)) ? 1 : 0) != 0;
     fence_after();
   }
-  if (!ok) atomicExch(&g_tc_timeout, 1);
+  cp_wait_all();
+  if (!ok && tid == 0) atomicExch(&g_tc_timeout, 1);
 
   // epilogue: warp w holds accumulator rows 32w .. 32w+31 (TMEM lanes)
   const int row = r0 + warp * 32 + lane;
   const int oidx = (row < nrows) ? rowidx[row] : -1;
   for (int cb = 0; cb < N; cb += 16) {
     uint32_t r[16];
-    if (ncols > 0 && ok) {
+    if (nchunks > 0 && ok) {
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, r);
     } else {
 #pragma unroll
