@@ -132,7 +132,7 @@ def get_operator(a, rank, ws):
 
 def config_of(a, info, l2):
     return {"workload": f"2D generalized Radon transform (Example 3), n={a.n} (N={a.n * a.n}), direct "
-                        f"inverse apply f = G K* u, complex64, b={a.b} RHS per step",
+                        f"inverse apply f = G K* u, complex64 (FP32 arithmetic), b={a.b} RHS per step",
             "kind": a.kind, "n": a.n, "N": a.n * a.n, "b": a.b, "eps_bf": a.eps_bf, "eps_hif": a.eps_hif,
             "L": info.get("L"), "LH": info.get("LH"), "root": info.get("root"), "l2": l2,
             "parallelism": "replicas"}
@@ -311,6 +311,39 @@ def main():
         except Exception as exc:  # reported, not hidden: the variant line says why it is missing
             variants[name] = {"error": str(exc)[:200]}
 
+    # solve latency to ||u - K-dot f|| <= 1e-10 ||u||: the plain FP64 path (PCG on K*K with G, FP64
+    # factors, one right-hand side per call) against FP64-residual iterative refinement whose
+    # corrections run on the tensor cores, on batches of b right-hand sides
+    solves = {}
+    u128 = binding.colmajor(torch.from_numpy(u_np).cuda())
+
+    def timed_solves(tag, make_u, reps, **kw):
+        lat, its, rr = [], [], []
+        for _ in range(reps):
+            uu = make_u()
+            torch.cuda.synchronize()
+            s0 = time.perf_counter()
+            ff, infos = op.solve(uu, tol=1e-10, maxit=200, **kw)
+            lat.append(1000 * (time.perf_counter() - s0))
+            its += [i for i, _, _ in infos]
+            rr += [r for _, r, _ in infos]
+        nb = make_u().shape[1] if make_u().dim() == 2 else 1
+        lat.sort()
+        solves[tag] = {"b": nb, "p50_ms": round(statistics.median(lat), 3),
+                       "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+                       "rhs_per_s": round(nb * 1000.0 / statistics.mean(lat), 2),
+                       "iters_max": max(its), "relres_max": max(rr), "solves": reps}
+
+    try:
+        cols = iter(range(10 ** 9))
+        timed_solves("plain_fp64_pcg_b1", lambda: binding.colmajor(u128[:, next(cols) % b:][:, :1].contiguous()),
+                     6, method=binding.FIO_PCG, inner=binding.FIO_P64)
+        timed_solves(f"ir_bf16_inner_b{b}", lambda: u128, 3, method=binding.FIO_IR, inner=binding.FIO_PBF16)
+        timed_solves(f"ir_tf32_inner_b{b}", lambda: u128, 3, method=binding.FIO_IR, inner=binding.FIO_PTF32)
+        timed_solves(f"gmres_fp32_precond_b{b}", lambda: u128, 3, method=binding.FIO_GMRES, inner=binding.FIO_P32)
+    except Exception as exc:
+        solves["error"] = str(exc)[:200]
+
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     uh = torch.from_numpy(u_np.astype(np.complex64)).t().contiguous().pin_memory()  # (b, N) rows = RHS
     fh = torch.empty_like(uh).pin_memory()
@@ -336,7 +369,7 @@ def main():
                 "data": "synthetic", "config": config_of(a, info, "flushed before every step (256 MB write)"),
                 "rhs_N_per_s": round(value * N, 1), "wall_ms_per_step": round(1000 * t_wall / a.steps, 4),
                 "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-                "cpu_baseline": cpu, "stages": stage_rows, "variants": variants,
+                "cpu_baseline": cpu, "stages": stage_rows, "variants": variants, "solve_latency": solves,
                 "factors": {"P_K": tot["P_K"], "P_G": tot["P_G"], "padded_K": tot["padded_K"],
                             "padded_G": tot["padded_G"], "bytes_c64": 8 * (tot["padded_K"] + tot["padded_G"]),
                             "build_s": {k: info.get(k) for k in ("t_bf", "t_peel", "t_hif", "t_total")}}}

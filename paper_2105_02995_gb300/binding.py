@@ -181,6 +181,23 @@ class Operator:
         FIO_PBF16 for the tensor-core stage products on complex64 vectors."""
         return self._apply(self._lib.fio_apply_inv, "fio_apply_inv", u, f, precision)
 
+    def capture_inv(self, u, f, precision=None):
+        """A CUDA graph of one fio_apply_inv(u -> f) on these buffers; replay it with .replay().
+
+        A first call on a side stream sizes the operator's scratch pool, so the captured call
+        neither allocates nor synchronises (both are illegal while a stream is being captured)."""
+        import torch
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.apply_inv(u, f, precision)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.apply_inv(u, f, precision)
+        return g
+
     def apply_inv_host(self, u: np.ndarray, f: np.ndarray | None = None) -> np.ndarray:
         """Host-buffer direct solve: numpy (N, b) Fortran-ordered complex128/complex64 arrays."""
         u = np.asfortranarray(u)
