@@ -120,10 +120,12 @@ def allmax(ws, v):
 
 
 def get_operator(a, rank, ws):
-    """Rank 0 builds (or reuses the on-disk cache); the others read the cache after a barrier."""
+    """Rank 0 builds (or reuses the on-disk cache); the others read the cache after a barrier.
+    The build's peeling probes run on the GPU when there is one."""
+    import torch
     from paper_2105_02995_gb300.builder.__main__ import build_cached
     if rank == 0:
-        buf, info = build_cached(a.kind, a.n, a.eps_bf, a.eps_hif, gpu=True, verbose=True)
+        buf, info = build_cached(a.kind, a.n, a.eps_bf, a.eps_hif, gpu=torch.cuda.is_available(), verbose=True)
     barrier(ws)
     if rank != 0:
         buf, info = build_cached(a.kind, a.n, a.eps_bf, a.eps_hif, gpu=False, verbose=False)

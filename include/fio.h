@@ -183,6 +183,14 @@ int fio_apply_profiled(fio_op op, int which, const void* x, void* y, int64_t ld,
 int fio_apply_inv_noalloc(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
                           int precision, void* stream);
 
+/* Self-test of the bounded device waits (no paper counterpart): launches nblocks CTAs that each
+ * wait on an mbarrier nothing arrives at, with a limit of limit_us microseconds (1..1e6).  Every
+ * wait must give up and return; *gave_up (host) receives how many did.  Returns FIO_ETIMEOUT when
+ * the timeouts were reported as the kernels report them (the expected outcome), FIO_EINVAL for
+ * bad arguments, FIO_ECUDA / FIO_ENOMEM otherwise.  Synchronises `stream`; leaves the device
+ * usable.  This is how the library's failure path is tested without a device fault or hang. */
+int fio_selftest_wait(int limit_us, int nblocks, int* gave_up, void* stream);
+
 /* Free the device copies and scratch of op (synchronises the device first).  NULL is a no-op. */
 int fio_release(fio_op op);
 

@@ -26,7 +26,7 @@ STATUS = {0: "FIO_OK", -1: "FIO_EINVAL", -2: "FIO_ENOMEM", -3: "FIO_EBADFACTORS"
           -4: "FIO_ENOCONV", -5: "FIO_ETIMEOUT", -6: "FIO_ECUDA", -7: "FIO_ENOTSUP"}
 SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv",
            "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_apply_profiled",
-           "fio_apply_inv_noalloc", "fio_release", "fio_strerror"]
+           "fio_apply_inv_noalloc", "fio_selftest_wait", "fio_release", "fio_strerror"]
 
 _lib = None
 
@@ -66,6 +66,7 @@ def load(path: str = LIB_PATH):
     lib.fio_launch_count.argtypes = [vp, c_int, c_int, ctypes.POINTER(c_int)]
     lib.fio_apply_profiled.argtypes = [vp, c_int, vp, vp, i64, c_int, c_int, c_int, vp,
                                        ctypes.POINTER(ctypes.c_float), c_int, ctypes.POINTER(c_int)]
+    lib.fio_selftest_wait.argtypes = [c_int, c_int, ctypes.POINTER(c_int), vp]
     lib.fio_release.argtypes = [vp]
     lib.fio_strerror.argtypes = [c_int]
     lib.fio_strerror.restype = ctypes.c_char_p

@@ -833,3 +833,26 @@ extern "C" int fio_apply_inv_noalloc(fio_op op, const void* u, void* f, int64_t 
                              (float2*)(p + per), (float2*)(p + 2 * per), s);
   return finish(s);
 }
+
+// ---------------------------------------------------------------------------------------------
+// fio_selftest_wait: exercises the bounded-wait path of the tensor-core kernel (see fio.h)
+// ---------------------------------------------------------------------------------------------
+extern "C" int fio_selftest_wait(int limit_us, int nblocks, int* gave_up, void* stream) {
+  if (limit_us <= 0 || limit_us > 1000000 || nblocks <= 0 || nblocks > 4096 || !gave_up) return FIO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return FIO_ENOMEM;
+  }
+  cudaMemsetAsync(d, 0, sizeof(int), s);
+  k_wait_selftest<<<nblocks, 32, 0, s>>>((uint64_t)limit_us * 1000ull, d);
+  int rc = FIO_OK;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(gave_up, d, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    rc = FIO_ECUDA;
+  cudaFree(d);
+  if (rc == FIO_OK && fio_tc_timeout_reset() > 0 && *gave_up > 0) rc = FIO_ETIMEOUT;
+  return rc;
+}

@@ -54,11 +54,11 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (!mbar_try(bar, parity))
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   return true;
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -306,6 +306,20 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
   fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, ncol_tmem);
+}
+
+// Self-test of the bounded wait: every CTA waits on an mbarrier that nothing arrives at, with a
+// limit of limit_ns; the wait must give up, record the timeout and return.
+__global__ void k_wait_selftest(uint64_t limit_ns, int* gave_up) {
+  using namespace tc;
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, limit_ns);
+  if (!ok && threadIdx.x == 0) {
+    atomicAdd(gave_up, 1);
+    atomicExch(&g_tc_timeout, 1);
+  }
 }
 
 // block-wise transpose of the complex64 copy: out block (C x R) = in block (R x C)^T
