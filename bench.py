@@ -35,6 +35,25 @@ SMS, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12  # 80.5 TFLOP/s (FFMA = 2 flops)
 
 
+def measured_traffic():
+    """DRAM bytes per apply of the stage kernel from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken (the summary records its hash)."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "traffic_ex3_n256_b32.md")
+    src = os.path.join(ROOT, "paper_2105_02995_gb300", "csrc", "fio_kernels.cuh")
+    try:
+        text = open(prof).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if f"kernel_source_sha256_16: {h}" not in text:
+            return None
+        for line in text.splitlines():
+            if line.startswith("traffic_bytes_per_apply:"):
+                return int(line.split(":")[1])
+    except OSError:
+        return None
+    return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -286,8 +305,11 @@ def main():
     peaks, src = measured_peaks()
     achieved = kern_flops / (kern_time / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
-            "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
-            "kernel": "k_stage_mm (every stage launch of one apply, float2, b=32)",
+            "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+            "traffic": measured_traffic() if (a.n == 256 and b == 32 and a.kind == "ex3") else None,
+            "traffic_unit": "DRAM bytes per apply (all stage launches), ncu",
+            "kernel": "k_stage_mm_pipe (every stage launch of one apply, float2, b=32)",
+            "algorithmic_bytes_per_apply": int(kern_bytes),
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
             "hbm_view": {"achieved_gbs": round(kern_bytes / (kern_time / 1e3) / 1e9, 1),
                          "peak_gbs": peaks.get("hbm_gbs"), "peak_source": src},
