@@ -23,9 +23,18 @@
  * FIO_PTF32 and FIO_PBF16 run the stage products on the tensor cores (tcgen05) with FP32
  * accumulation: TF32 products of the complex64 copy, or products of a bfloat16 copy of the
  * factors with bfloat16-rounded vectors; both take complex64 vectors and are meant as the inner
- * precision of an iterative refinement (their rounding is ~1e-3 resp. ~4e-3 per stage).  With
- * fewer than 8 right-hand sides they fall back to the FP32 CUDA-core kernels.  The vector dtype
- * must match the precision (C128 with P64, C64 with the others); other pairs return FIO_EINVAL.
+ * precision of an iterative refinement (their rounding is ~1e-3 resp. ~4e-3 per stage).
+ * FIO_PTF32X3 is FP32-accurate on the TF32 tensor cores: each operand value is split into a TF32
+ * head and a TF32 tail and a product is summed as head*head + head*tail + tail*head (three MMAs
+ * per step, FP32 accumulation; the dropped tail*tail term is ~2^-22 relative); same factors and
+ * vectors as FIO_PTF32.  With fewer than 8 right-hand sides the tensor-core precisions fall back
+ * to the FP32 CUDA-core kernels.  FIO_PDF takes complex128 vectors and applies a double-float copy
+ * of the factors (each FP64 entry as an unevaluated sum of two floats, 48-bit significand) with
+ * compensated (twice-working-precision) accumulation on the FP32 CUDA cores: FP64-class results
+ * (~1e-14 relative per stage) at the FP32 pipes' rate, for the outer residual of iterative
+ * refinement (GB300's FP64 rate is a small fraction of its FP32 rate); it adds two conversion
+ * launches per apply and is not accepted by fio_apply_inv_noalloc.  The vector dtype
+ * must match the precision (C128 with P64 and PDF, C64 with the others); other pairs return FIO_EINVAL.
  *
  * STREAMS AND SCRATCH.  Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
  * default stream) unless stated otherwise.  Each operator owns a scratch pool (device memory for
@@ -83,19 +92,22 @@ extern "C" {
 typedef struct fio_op_s* fio_op;
 
 typedef enum { FIO_C128 = 0, FIO_C64 = 1 } fio_dtype;
-typedef enum { FIO_P64 = 0, FIO_P32 = 1, FIO_PTF32 = 2, FIO_PBF16 = 3 } fio_precision;
+typedef enum { FIO_P64 = 0, FIO_P32 = 1, FIO_PTF32 = 2, FIO_PBF16 = 3, FIO_PTF32X3 = 4, FIO_PDF = 5 } fio_precision;
 typedef enum { FIO_DIRECT = 0, FIO_PCG = 1, FIO_GMRES = 2, FIO_IR = 3 } fio_method;
 
 #define FIO_MASK_P64 1u
 #define FIO_MASK_P32 2u
 #define FIO_MASK_TC 4u /* tensor-core copies: block-transposed complex64 and bf16 (both orientations) */
+#define FIO_MASK_DF 8u /* double-float copy of the factors (FIO_PDF)                                  */
 
 typedef struct {
   int method;    /* fio_method                                                                 */
-  int inner;     /* fio_precision of the preconditioner / inner correction (FIO_IR: P32 or P64) */
+  int inner;     /* fio_precision of the preconditioner / inner correction (any fio_precision)  */
   double tol;    /* stop when ||u - K-dot f|| <= tol ||u|| for every right-hand side           */
   int maxit;     /* iteration cap (outer iterations for FIO_IR)                                 */
   int restart;   /* GMRES restart length (FIO_GMRES, and the inner GMRES of FIO_IR)             */
+  int outer;     /* fio_precision of the residuals u - K-dot f on complex128 vectors: FIO_P64   */
+                 /* (0, FP64 arithmetic) or FIO_PDF (double-float arithmetic)                   */
 } fio_solve_opts;
 
 typedef struct {
@@ -105,8 +117,8 @@ typedef struct {
 } fio_solve_info;
 
 /* Validate `packed` (nbytes host bytes; the layout above), copy it to the device of the current
- * CUDA context and derive the precision copies named by precisions_mask (FIO_MASK_P64 and/or
- * FIO_MASK_P32; 0 means both).  The caller keeps ownership of `packed` and may free it on return
+ * CUDA context and derive the precision copies named by precisions_mask (FIO_MASK_P64, FIO_MASK_P32,
+ * FIO_MASK_TC (needs P32), FIO_MASK_DF; 0 means all four).  The caller keeps ownership of `packed` and may free it on return
  * (the copy is synchronous with respect to the host).  On success *out owns the device copies
  * until fio_release.  Errors: FIO_EINVAL (null args), FIO_EBADFACTORS, FIO_ENOMEM, FIO_ECUDA. */
 int fio_upload_factors(const void* packed, size_t nbytes, unsigned precisions_mask, void* stream,
@@ -137,13 +149,33 @@ int fio_apply_inv_host(fio_op op, const void* u_host, void* f_host, int64_t ld, 
  *   FIO_DIRECT  f = G-dot K-dot* u (no iteration);
  *   FIO_PCG     CG on K-dot* K-dot f = K-dot* u preconditioned with G-dot (the paper's solver);
  *   FIO_GMRES   GMRES on K-dot f = u right-preconditioned with G-dot K-dot*;
- *   FIO_IR      iterative refinement: FP64 residual r = u - K-dot f, correction G-dot K-dot* r in
+ *   FIO_IR      iterative refinement: residual r = u - K-dot f on complex128 vectors in
+ *               opts->outer precision (FP64 or double-float), correction G-dot K-dot* r in
  *               opts->inner precision, FP64 update f += d.
+ * Every method computes its true residuals u - K-dot f in opts->outer precision (PCG and GMRES
+ * run their Krylov products in FP64 whatever opts->outer is).  An all-zero initial guess is
+ * detected and its residual taken as u without an apply.
  * f holds the initial guess on entry (zero it for none) and the solution on return.  dtype must
  * be FIO_C128 (FP64 solution).  info_host (may be NULL) receives one record per right-hand side;
  * the call synchronises `stream`.  Returns FIO_OK, FIO_ENOCONV, or an error code. */
 int fio_solve(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
               const fio_solve_opts* opts, fio_solve_info* info_host, void* stream);
+
+/* Autotuner (batching: the tile shape of every stage launch picked by measurement).  For b
+ * right-hand sides in `precision`, time each candidate kernel variant of every stage launch
+ * (forward and adjoint, on the operator's own factors and zeroed scratch vectors; best of three
+ * launches after one warm-up) and keep the fastest for that stage, direction, arithmetic type
+ * and right-hand-side bucket (b <= 4, 5-8, 9-16, 17-32, > 32).  Later applies of the same type
+ * and bucket use the choice; untuned ones keep the built-in choice by b.  Variants: 1..7 tile
+ * shapes <TX,TB,TR> of the tiled stage kernel (1 <8,1,2>, 2 <16,1,4>, 3 <16,2,4>, 4 <8,2,2>,
+ * 5 <8,4,2>, 6 <32,1,8>, 7 <16,4,4>: TX x TB right-hand sides and 64 rows per 256-thread CTA),
+ * 8 the few-right-hand-side kernel (b <= 4); 0 = not tuned (tensor-core launches, empty stages).
+ * Every variant sums each output's terms in the same order, except 8 (tree reductions), so
+ * results for b >= 5 do not depend on the choice.  choices (may be NULL when cap == 0) receives
+ * the variant per stage launch in stage order, forward before adjoint (the root: forward
+ * only); *nchoices (may be NULL) their number.  Synchronises `stream`; must not run
+ * concurrently with other calls on the operator. */
+int fio_autotune(fio_op op, int b, int precision, void* stream, int* choices, int cap, int* nchoices);
 
 /* Operator facts: dimension, grid size n, N = n^d, device bytes held (factors + scratch). */
 int fio_query(fio_op op, int* d, int64_t* n, int64_t* N, size_t* device_bytes);

@@ -19,14 +19,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfio.so")
 
 FIO_C128, FIO_C64 = 0, 1
-FIO_P64, FIO_P32, FIO_PTF32, FIO_PBF16 = 0, 1, 2, 3
+FIO_P64, FIO_P32, FIO_PTF32, FIO_PBF16, FIO_PTF32X3, FIO_PDF = 0, 1, 2, 3, 4, 5
 FIO_DIRECT, FIO_PCG, FIO_GMRES, FIO_IR = 0, 1, 2, 3
-FIO_MASK_P64, FIO_MASK_P32, FIO_MASK_TC = 1, 2, 4
+FIO_MASK_P64, FIO_MASK_P32, FIO_MASK_TC, FIO_MASK_DF = 1, 2, 4, 8
 STATUS = {0: "FIO_OK", -1: "FIO_EINVAL", -2: "FIO_ENOMEM", -3: "FIO_EBADFACTORS",
           -4: "FIO_ENOCONV", -5: "FIO_ETIMEOUT", -6: "FIO_ECUDA", -7: "FIO_ENOTSUP"}
 SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv",
            "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_apply_profiled",
-           "fio_apply_inv_noalloc", "fio_selftest_wait", "fio_release", "fio_strerror"]
+           "fio_apply_inv_noalloc", "fio_selftest_wait", "fio_autotune", "fio_release", "fio_strerror"]
 
 _lib = None
 
@@ -39,7 +39,7 @@ class FioError(RuntimeError):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("inner", ctypes.c_int), ("tol", ctypes.c_double),
-                ("maxit", ctypes.c_int), ("restart", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("outer", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -67,6 +67,7 @@ def load(path: str = LIB_PATH):
     lib.fio_apply_profiled.argtypes = [vp, c_int, vp, vp, i64, c_int, c_int, c_int, vp,
                                        ctypes.POINTER(ctypes.c_float), c_int, ctypes.POINTER(c_int)]
     lib.fio_selftest_wait.argtypes = [c_int, c_int, ctypes.POINTER(c_int), vp]
+    lib.fio_autotune.argtypes = [vp, c_int, c_int, vp, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int)]
     lib.fio_release.argtypes = [vp]
     lib.fio_strerror.argtypes = [c_int]
     lib.fio_strerror.restype = ctypes.c_char_p
@@ -133,6 +134,15 @@ class Operator:
         _check(self._lib.fio_query(self.h, None, None, None, ctypes.byref(nb)), "fio_query")
         return nb.value
 
+    def autotune(self, b: int, precision: int):
+        """Pick every stage launch's kernel variant for b right-hand sides in `precision` by
+        timing (fio_autotune); returns the chosen variant per stage launch."""
+        cap = 4096
+        ch = (ctypes.c_int * cap)()
+        n = ctypes.c_int()
+        _check(self._lib.fio_autotune(self.h, b, precision, _stream(), ch, cap, ctypes.byref(n)), "fio_autotune")
+        return [ch[i] for i in range(min(n.value, cap))]
+
     def launches(self, which: str, b: int) -> int:
         k = {"K": 0, "Kadj": 1, "G": 2, "inv": 3}[which]
         out = ctypes.c_int()
@@ -168,18 +178,18 @@ class Operator:
                                             ms, cap, ctypes.byref(nm)), "fio_apply_profiled")
         return [ms[i] for i in range(nm.value)]
 
-    def apply_K(self, x, y=None):
-        return self._apply(self._lib.fio_apply_K, "fio_apply_K", x, y)
+    def apply_K(self, x, y=None, precision=None):
+        return self._apply(self._lib.fio_apply_K, "fio_apply_K", x, y, precision)
 
-    def apply_Kadj(self, x, y=None):
-        return self._apply(self._lib.fio_apply_Kadj, "fio_apply_Kadj", x, y)
+    def apply_Kadj(self, x, y=None, precision=None):
+        return self._apply(self._lib.fio_apply_Kadj, "fio_apply_Kadj", x, y, precision)
 
-    def apply_G(self, x, y=None):
-        return self._apply(self._lib.fio_apply_G, "fio_apply_G", x, y)
+    def apply_G(self, x, y=None, precision=None):
+        return self._apply(self._lib.fio_apply_G, "fio_apply_G", x, y, precision)
 
     def apply_inv(self, u, f=None, precision=None):
         """f = G-dot K-dot* u; precision defaults to the dtype's (P64 / P32), or FIO_PTF32 /
-        FIO_PBF16 for the tensor-core stage products on complex64 vectors."""
+        FIO_PBF16 / FIO_PTF32X3 for the tensor-core stage products on complex64 vectors."""
         return self._apply(self._lib.fio_apply_inv, "fio_apply_inv", u, f, precision)
 
     def capture_inv(self, u, f, precision=None):
@@ -220,15 +230,16 @@ class Operator:
         return f
 
     def solve(self, u, f=None, method: int = FIO_GMRES, inner: int = FIO_P64, tol: float = 1e-10,
-              maxit: int = 100, restart: int = 20):
-        """Iterative solve of K-dot f = u (complex128 tensors); returns (f, list of (iters, relres, status))."""
+              maxit: int = 100, restart: int = 20, outer: int = FIO_P64):
+        """Iterative solve of K-dot f = u (complex128 tensors); returns (f, list of (iters, relres, status)).
+        outer = FIO_PDF computes the true residuals in double-float arithmetic."""
         import torch
         if f is None:
             f = torch.zeros_like(u)
         dt, prec, b, ld = _vec(u, self.N)
         if dt != FIO_C128:
             raise ValueError("fio_solve takes complex128 vectors")
-        opts = SolveOpts(method, inner, tol, maxit, restart)
+        opts = SolveOpts(method, inner, tol, maxit, restart, outer)
         infos = (SolveInfo * max(b, 1))()
         rc = self._lib.fio_solve(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(f.data_ptr()),
                                  ld, b, dt, ctypes.byref(opts), infos, _stream())

@@ -66,7 +66,7 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
                                   fio_op* out) {
   if (!packed || !out) return FIO_EINVAL;
   *out = nullptr;
-  if (mask == 0) mask = FIO_MASK_P64 | FIO_MASK_P32 | FIO_MASK_TC;
+  if (mask == 0) mask = FIO_MASK_P64 | FIO_MASK_P32 | FIO_MASK_TC | FIO_MASK_DF;
   const uint8_t* p = (const uint8_t*)packed;
   if (nbytes < kHeader || memcmp(p, "FIOPACK1", 8) != 0) return FIO_EBADFACTORS;
   const uint32_t version = rd<uint32_t>(p, 8), d = rd<uint32_t>(p, 12);
@@ -219,6 +219,14 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
     }
     op->arena32_bytes = m_elems * sizeof(float2) + 256;
   }
+  if (mask & FIO_MASK_DF) {
+    if (cudaMalloc(&op->arena_df, m_elems * sizeof(dfc) + 256) != cudaSuccess) {
+      cudaGetLastError();
+      fio_release(op);
+      return FIO_ENOMEM;
+    }
+    op->arena_df_bytes = m_elems * sizeof(dfc) + 256;
+  }
   size_t off32 = 0;
   for (auto& st : op->st) {
     const size_t ne = (size_t)st.nblk * st.R * st.C;
@@ -231,8 +239,13 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
       if (ne) {
         k_cast_c128_c64<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(st.M64, dst, ne);
       }
-      off32 += ne;
     }
+    if (op->arena_df) {
+      dfc* dst = (dfc*)op->arena_df + off32;
+      st.Mdf = dst;
+      if (ne) k_split_df<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(st.M64, dst, ne);
+    }
+    off32 += ne;
   }
   if ((mask & FIO_MASK_TC) && op->arena32) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -283,6 +296,7 @@ extern "C" int fio_release(fio_op op) {
   cudaDeviceSynchronize();
   if (op->arena) cudaFree(op->arena);
   if (op->arena32) cudaFree(op->arena32);
+  if (op->arena_df) cudaFree(op->arena_df);
   if (op->meta) cudaFree(op->meta);
   if (op->arena_tc) cudaFree(op->arena_tc);
   if (op->scratch) cudaFree(op->scratch);
@@ -298,7 +312,7 @@ extern "C" int fio_query(fio_op op, int* d, int64_t* n, int64_t* N, size_t* devi
   if (n) *n = op->n;
   if (N) *N = op->N;
   if (device_bytes)
-    *device_bytes = op->arena_bytes + op->arena32_bytes + op->arena_tc_bytes + op->meta_bytes +
+    *device_bytes = op->arena_bytes + op->arena32_bytes + op->arena_tc_bytes + op->arena_df_bytes + op->meta_bytes +
                     op->scratch_bytes + op->solver_bytes;
   return FIO_OK;
 }
@@ -362,10 +376,12 @@ inline void mark(cudaStream_t s) {
 template <typename V> const V* stage_M(const Stage& st);
 template <> const double2* stage_M<double2>(const Stage& st) { return st.M64; }
 template <> const float2* stage_M<float2>(const Stage& st) { return st.M32; }
+template <> const dfc* stage_M<dfc>(const Stage& st) { return st.Mdf; }
 
 template <typename V> struct ChunkK;
 template <> struct ChunkK<double2> { static constexpr int v = 16; };
 template <> struct ChunkK<float2> { static constexpr int v = 32; };
+template <> struct ChunkK<dfc> { static constexpr int v = 16; };
 
 template <typename V, bool ADJ, int TX, int TB, int TR>
 void launch_mm(StageArgs<V> a, cudaStream_t s) {
@@ -406,24 +422,81 @@ bool pipe_ok(const StageArgs<V>& a) {
          ((uintptr_t)a.M & 15) == 0 && ((uintptr_t)a.x & 15) == 0;
 }
 
+// few right-hand sides: k_stage_vec when the tile's gathered input fits in shared memory (false:
+// the caller falls back to the tiled kernel)
+template <typename V, bool ADJ, int B>
+bool launch_vec_b(StageArgs<V> a, cudaStream_t s) {
+  static int cap = 48 * 1024;  // dynamic shared memory allowed so far for this instantiation
+  const long long slots = (long long)(ADJ ? std::max<int>(a.R, 256) : a.C) * B;
+  const long long need = slots * (long long)sizeof(V);
+  if (need > 200 * 1024) return false;
+  if (need > cap) {
+    if (cudaFuncSetAttribute(k_stage_vec<V, ADJ, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cap = (int)need;
+  }
+  const int nrows = ADJ ? a.C : a.R;
+  a.ntiles = (nrows + kTileRows - 1) / kTileRows;
+  const long long ncta = a.tiles ? a.ntiles_list : (long long)a.nblk * a.ntiles;
+  if (ncta == 0) return true;
+  k_stage_vec<V, ADJ, B><<<(unsigned)ncta, 256, (size_t)need, s>>>(a);
+  return true;
+}
 template <typename V, bool ADJ>
-void launch_stage_dir(const StageArgs<V>& a, cudaStream_t s) {
+bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
+  switch (a.b) {
+    case 1: return launch_vec_b<V, ADJ, 1>(a, s);
+    case 2: return launch_vec_b<V, ADJ, 2>(a, s);
+    case 3: return launch_vec_b<V, ADJ, 3>(a, s);
+    case 4: return launch_vec_b<V, ADJ, 4>(a, s);
+    default: return false;
+  }
+}
+
+// ---- kernel variants (the autotuner's candidates) -----------------------------------------
+// 1..7: tile shapes <TX, TB, TR> of the tiled kernel (256 threads, 64-row tiles, TX x TB
+// right-hand sides per CTA): 1 <8,1,2>, 2 <16,1,4>, 3 <16,2,4>, 4 <8,2,2>, 5 <8,4,2>,
+// 6 <32,1,8>, 7 <16,4,4>; 8: k_stage_vec (b <= 4).  Shapes 2..7 need the pipelined kernel's
+// layout (row-major, 16-byte aligned rows); shape 1 falls back to the plain tiled kernel.
+inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : (b <= 32 ? 3 : 4))); }
+// candidates per bucket, the built-in choice first
+constexpr int kCand[5][5] = {{8, 1, 0, 0, 0}, {1, 2, 0, 0, 0}, {2, 4, 3, 0, 0}, {3, 5, 6, 0, 0}, {3, 5, 6, 7, 0}};
+
+// launch with variant `var`; false when it does not apply to this launch
+template <typename V, bool ADJ>
+bool launch_variant(const StageArgs<V>& a, cudaStream_t s, int var) {
+  const bool pipe = pipe_ok(a);
+  switch (var) {
+    case 1:
+      if (pipe) launch_pipe<V, ADJ, 8, 1, 2>(a, s);
+      else launch_mm<V, ADJ, 8, 1, 2>(a, s);
+      return true;
+    case 2: if (!pipe) return false; launch_pipe<V, ADJ, 16, 1, 4>(a, s); return true;
+    case 3: if (!pipe) return false; launch_pipe<V, ADJ, 16, 2, 4>(a, s); return true;
+    case 4: if (!pipe) return false; launch_pipe<V, ADJ, 8, 2, 2>(a, s); return true;
+    case 5: if (!pipe) return false; launch_pipe<V, ADJ, 8, 4, 2>(a, s); return true;
+    case 6: if (!pipe) return false; launch_pipe<V, ADJ, 32, 1, 8>(a, s); return true;
+    case 7: if (!pipe) return false; launch_pipe<V, ADJ, 16, 4, 4>(a, s); return true;
+    case 8: return a.b <= kVecMaxRhs && launch_vec<V, ADJ>(a, s);
+    default: return false;
+  }
+}
+
+// var: the tuned variant of this launch (0 = none): else the built-in choice by b
+template <typename V, bool ADJ>
+void launch_stage_dir(const StageArgs<V>& a, cudaStream_t s, int var) {
+  if (var > 0 && launch_variant<V, ADJ>(a, s, var)) return;
   if (a.b >= 5 && pipe_ok(a)) {
     if (a.b <= 8) launch_pipe<V, ADJ, 8, 1, 2>(a, s);
     else if (a.b <= 16) launch_pipe<V, ADJ, 16, 1, 4>(a, s);
     else launch_pipe<V, ADJ, 16, 2, 4>(a, s);
     return;
   }
-  if (a.b <= 4) {
-    if (!ADJ) {
-      const long long warps = (long long)a.nblk * a.R;
-      k_stage_mv_fwd<V><<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(a);
-    } else {
-      int threads = a.C < 256 ? ((a.C + 31) / 32) * 32 : 256;
-      dim3 grid((unsigned)((a.C + threads - 1) / threads), (unsigned)a.nblk);
-      k_stage_mv_adj<V><<<grid, threads, 0, s>>>(a);
-    }
-  } else if (a.b <= 8) {
+  if (a.b <= kVecMaxRhs && launch_vec<V, ADJ>(a, s)) return;
+  if (a.b <= 8) {  // also b <= 4 on blocks too wide for k_stage_vec's shared-memory gather
     launch_mm<V, ADJ, 8, 1, 2>(a, s);
   } else if (a.b <= 16) {
     launch_mm<V, ADJ, 16, 1, 4>(a, s);
@@ -432,32 +505,35 @@ void launch_stage_dir(const StageArgs<V>& a, cudaStream_t s) {
   }
 }
 
-// stage arithmetic of the float2 path: 0 FP32 CUDA cores, 1 TF32 / 2 BF16 tensor cores (tcgen05);
-// set for the duration of one public call (TcMode), read by launch_stage
+// stage arithmetic of the float2 path: 0 FP32 CUDA cores, or a k_stage_tc operand mode on the
+// tensor cores (kTcTF32, kTcBF16, kTcX3 = split TF32); set for the duration of one public call
+// (TcMode), read by launch_stage
 thread_local int g_tc_mode = 0;
 struct TcMode {
   int prev;
   explicit TcMode(int m) : prev(g_tc_mode) { g_tc_mode = m; }
   ~TcMode() { g_tc_mode = prev; }
 };
-inline int tc_mode_of(int prec) { return prec == FIO_PTF32 ? 1 : (prec == FIO_PBF16 ? 2 : 0); }
+inline int tc_mode_of(int prec) {
+  return prec == FIO_PTF32 ? kTcTF32 : (prec == FIO_PBF16 ? kTcBF16 : (prec == FIO_PTF32X3 ? kTcX3 : 0));
+}
 
-template <bool ADJ, bool BF16>
+template <bool ADJ, int MODE>
 void launch_tc_dir(const TcArgs& a, int ncta, cudaStream_t s) {
   static int cap = 48 * 1024;  // dynamic shared memory allowed without opting in
-  const int need = tc_smem_bytes(BF16, a.nmax, a.ncmax);
+  const int need = tc_smem_bytes(MODE, a.nmax, a.ncmax);
   if (need > cap) {
-    if (cudaFuncSetAttribute(k_stage_tc<ADJ, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, need) ==
+    if (cudaFuncSetAttribute(k_stage_tc<ADJ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, need) ==
         cudaSuccess)
       cap = need;
   }
   dim3 grid((unsigned)ncta, (unsigned)((a.b + kTcMaxRhs - 1) / kTcMaxRhs));
-  k_stage_tc<ADJ, BF16><<<grid, 128, tc_smem_bytes(BF16, a.nmax, a.ncmax), s>>>(a);
+  k_stage_tc<ADJ, MODE><<<grid, 128, need, s>>>(a);
 }
 
 void launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long long xcs, float2* y,
                long long yrs, long long ycs, int b, cudaStream_t s) {
-  const bool bf = g_tc_mode == 2;
+  const bool bf = g_tc_mode == kTcBF16;
   TcArgs a;
   if (!adj) {
     a.A = bf ? (const void*)st.Mbf : (const void*)st.M32;
@@ -486,8 +562,14 @@ void launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long l
   a.stage_x = (xcs == 1 && xrs % 2 == 0 && b % 2 == 0 && ((uintptr_t)x & 15) == 0) ? 1 : 0;
   a.ncmax = adj ? (int)st.R : (int)st.C;  // gather list length per block (forward: in, adjoint: out)
   if (ncta == 0) return;
-  if (adj) bf ? launch_tc_dir<true, true>(a, ncta, s) : launch_tc_dir<true, false>(a, ncta, s);
-  else bf ? launch_tc_dir<false, true>(a, ncta, s) : launch_tc_dir<false, false>(a, ncta, s);
+  switch (g_tc_mode * 2 + (adj ? 1 : 0)) {
+    case 2 * kTcTF32: launch_tc_dir<false, kTcTF32>(a, ncta, s); break;
+    case 2 * kTcTF32 + 1: launch_tc_dir<true, kTcTF32>(a, ncta, s); break;
+    case 2 * kTcBF16: launch_tc_dir<false, kTcBF16>(a, ncta, s); break;
+    case 2 * kTcBF16 + 1: launch_tc_dir<true, kTcBF16>(a, ncta, s); break;
+    case 2 * kTcX3: launch_tc_dir<false, kTcX3>(a, ncta, s); break;
+    default: launch_tc_dir<true, kTcX3>(a, ncta, s); break;
+  }
 }
 
 template <typename V>
@@ -499,14 +581,14 @@ bool use_tc<float2>(const Stage& st, int b) {
   return g_tc_mode != 0 && b >= 8 && st.M32t != nullptr;
 }
 
+template <typename V> constexpr int type_index();
+template <> constexpr int type_index<double2>() { return 0; }
+template <> constexpr int type_index<float2>() { return 1; }
+template <> constexpr int type_index<dfc>() { return 2; }
+
 template <typename V>
-void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long long xcs, V* y,
-                  long long yrs, long long ycs, int b, cudaStream_t s) {
-  if (st.nblk == 0) return;
-  if (use_tc<V>(st, b)) {
-    launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s);
-    return;
-  }
+StageArgs<V> stage_args(const Stage& st, bool adj, const V* x, long long xrs, long long xcs, V* y,
+                        long long yrs, long long ycs, int b) {
   StageArgs<V> a;
   a.M = stage_M<V>(st);
   a.in = st.in;
@@ -525,8 +607,21 @@ void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long lon
   a.dims = st.dims;
   a.tiles = adj ? st.tiles_adj : st.tiles_fwd;
   a.ntiles_list = adj ? st.ntiles_adj : st.ntiles_fwd;
-  if (adj) launch_stage_dir<V, true>(a, s);
-  else launch_stage_dir<V, false>(a, s);
+  return a;
+}
+
+template <typename V>
+void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long long xcs, V* y,
+                  long long yrs, long long ycs, int b, cudaStream_t s) {
+  if (st.nblk == 0) return;
+  if (use_tc<V>(st, b)) {
+    launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s);
+    return;
+  }
+  const StageArgs<V> a = stage_args<V>(st, adj, x, xrs, xcs, y, yrs, ycs, b);
+  const int var = st.var[type_index<V>()][adj ? 1 : 0][rhs_bucket(b)];
+  if (adj) launch_stage_dir<V, true>(a, s, var);
+  else launch_stage_dir<V, false>(a, s, var);
 }
 
 // one INPLACE stage on the row-major work vector W (scratch S has the same shape)
@@ -593,10 +688,12 @@ int check_args(fio_op op, const void* x, const void* y, int64_t ld, int b, int d
   if (!op || b < 0) return FIO_EINVAL;
   if (b > 0 && (!x || !y || x == y)) return FIO_EINVAL;
   if (ld < op->N) return FIO_EINVAL;
-  const bool c64prec = prec == FIO_P32 || prec == FIO_PTF32 || prec == FIO_PBF16;
-  if (!((dtype == FIO_C128 && prec == FIO_P64) || (dtype == FIO_C64 && c64prec))) return FIO_EINVAL;
+  const bool c64prec = prec == FIO_P32 || is_tc_precision(prec);
+  const bool c128prec = prec == FIO_P64 || prec == FIO_PDF;
+  if (!((dtype == FIO_C128 && c128prec) || (dtype == FIO_C64 && c64prec))) return FIO_EINVAL;
   if (c64prec && !op->arena32) return FIO_EINVAL;
-  if ((prec == FIO_PTF32 || prec == FIO_PBF16) && !op->arena_tc) return FIO_EINVAL;
+  if (prec == FIO_PDF && !op->arena_df) return FIO_EINVAL;
+  if (is_tc_precision(prec) && !op->arena_tc) return FIO_EINVAL;
   const size_t es = dtype == FIO_C128 ? 16 : 8;
   const uint8_t *xb = (const uint8_t*)x, *yb = (const uint8_t*)y;
   const size_t span = ((size_t)ld * (b > 0 ? b - 1 : 0) + op->N) * es;
@@ -613,14 +710,9 @@ int finish(cudaStream_t) {
 
 enum Which { W_K = 0, W_KADJ = 1, W_G = 2, W_INV = 3 };
 
+// the apply `w` from x to y (both column-major, leading dimension ld) with work arrays A, B, W
 template <typename V>
-int apply_t(fio_op op, Which w, const void* xv, void* yv, int64_t ld, int b, cudaStream_t s) {
-  void* bufs[5];
-  int rc = fio_scratch(op, b, sizeof(V), s, bufs);
-  if (rc) return rc;
-  V *A = (V*)bufs[0], *B = (V*)bufs[1], *W = (V*)bufs[2];
-  const V* x = (const V*)xv;
-  V* y = (V*)yv;
+void apply_core(fio_op op, Which w, const V* x, V* y, int64_t ld, int b, V* A, V* B, V* W, cudaStream_t s) {
   switch (w) {
     case W_K: bf_chain<V>(op, false, x, 1, ld, y, 1, ld, b, A, B, s); break;
     case W_KADJ: bf_chain<V>(op, true, x, 1, ld, y, 1, ld, b, A, B, s); break;
@@ -635,7 +727,37 @@ int apply_t(fio_op op, Which w, const void* xv, void* yv, int64_t ld, int b, cud
       to_col<V>(W, y, ld, op->N, b, s);
       break;
   }
+}
+
+template <typename V>
+int apply_t(fio_op op, Which w, const void* xv, void* yv, int64_t ld, int b, cudaStream_t s) {
+  void* bufs[5];
+  int rc = fio_scratch(op, b, sizeof(V), s, bufs);
+  if (rc) return rc;
+  apply_core<V>(op, w, (const V*)xv, (V*)yv, ld, b, (V*)bufs[0], (V*)bufs[1], (V*)bufs[2], s);
   return finish(s);
+}
+
+// FIO_PDF: complex128 vectors in and out, every stage in double-float arithmetic; the vectors are
+// split into double-floats on entry (work array X, leading dimension N) and summed back on exit
+int apply_df(fio_op op, Which w, const void* xv, void* yv, int64_t ld, int b, cudaStream_t s) {
+  void* bufs[5];
+  int rc = fio_scratch(op, b, sizeof(dfc), s, bufs);
+  if (rc) return rc;
+  dfc *X = (dfc*)bufs[3], *Y = (dfc*)bufs[4];
+  const long long n = op->N * (long long)b;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  k_c128_to_df<<<g, 256, 0, s>>>((const double2*)xv, ld, X, op->N, b);
+  apply_core<dfc>(op, w, X, Y, op->N, b, (dfc*)bufs[0], (dfc*)bufs[1], (dfc*)bufs[2], s);
+  k_df_to_c128<<<g, 256, 0, s>>>(Y, op->N, (double2*)yv, ld, b);
+  return finish(s);
+}
+
+int apply_prec(fio_op op, Which w, const void* x, void* y, int64_t ld, int b, int prec, cudaStream_t s) {
+  if (prec == FIO_P64) return apply_t<double2>(op, w, x, y, ld, b, s);
+  if (prec == FIO_PDF) return apply_df(op, w, x, y, ld, b, s);
+  TcMode m(tc_mode_of(prec));
+  return apply_t<float2>(op, w, x, y, ld, b, s);
 }
 
 int apply_any(fio_op op, Which w, const void* x, void* y, int64_t ld, int b, int dtype, int prec,
@@ -646,9 +768,7 @@ int apply_any(fio_op op, Which w, const void* x, void* y, int64_t ld, int b, int
   if (b == 0) return FIO_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaGetLastError() != cudaSuccess) return FIO_ECUDA;
-  if (prec == FIO_P64) return apply_t<double2>(op, w, x, y, ld, b, s);
-  TcMode m(tc_mode_of(prec));
-  return apply_t<float2>(op, w, x, y, ld, b, s);
+  return apply_prec(op, w, x, y, ld, b, prec, s);
 }
 
 }  // namespace
@@ -657,9 +777,7 @@ int apply_any(fio_op op, Which w, const void* x, void* y, int64_t ld, int b, int
 int fio_apply_internal(fio_op op, int which, const void* x, void* y, int64_t ld, int b, int prec,
                        cudaStream_t s) {
   if (b == 0) return FIO_OK;
-  if (prec == FIO_P64) return apply_t<double2>(op, (Which)which, x, y, ld, b, s);
-  TcMode m(tc_mode_of(prec));
-  return apply_t<float2>(op, (Which)which, x, y, ld, b, s);
+  return apply_prec(op, (Which)which, x, y, ld, b, prec, s);
 }
 
 int fio_tc_timeout_reset() {
@@ -689,10 +807,11 @@ extern "C" int fio_apply_inv(fio_op op, const void* u, void* f, int64_t ld, int 
 extern "C" int fio_apply_inv_host(fio_op op, const void* u_host, void* f_host, int64_t ld, int b,
                                   int dtype, int precision, void* stream) {
   if (!op || !u_host || !f_host || b < 0 || ld < op->N) return FIO_EINVAL;
-  if (!((dtype == FIO_C128 && precision == FIO_P64) ||
-        (dtype == FIO_C64 && (precision == FIO_P32 || precision == FIO_PTF32 || precision == FIO_PBF16))))
+  if (!((dtype == FIO_C128 && (precision == FIO_P64 || precision == FIO_PDF)) ||
+        (dtype == FIO_C64 && (precision == FIO_P32 || is_tc_precision(precision)))))
     return FIO_EINVAL;
-  if ((precision == FIO_PTF32 || precision == FIO_PBF16) && !op->arena_tc) return FIO_EINVAL;
+  if (is_tc_precision(precision) && !op->arena_tc) return FIO_EINVAL;
+  if (precision == FIO_PDF && !op->arena_df) return FIO_EINVAL;
   if (op->n_root == 0) return FIO_ENOTSUP;
   if (b == 0) return FIO_OK;
   cudaStream_t s = (cudaStream_t)stream;
@@ -744,11 +863,7 @@ extern "C" int fio_apply_profiled(fio_op op, int which, const void* x, void* y, 
   Marks m{ev.data() + 1, cap, 0};
   cudaEventRecord(ev[0], s);
   g_marks = &m;
-  {
-    TcMode mode(tc_mode_of(precision));
-    rc = precision == FIO_P64 ? apply_t<double2>(op, (Which)which, x, y, ld, b, s)
-                              : apply_t<float2>(op, (Which)which, x, y, ld, b, s);
-  }
+  rc = apply_prec(op, (Which)which, x, y, ld, b, precision, s);
   g_marks = nullptr;
   if (rc == FIO_OK) {
     const cudaError_t se = cudaStreamSynchronize(s);
@@ -762,6 +877,107 @@ extern "C" int fio_apply_profiled(fio_op op, int which, const void* x, void* y, 
     if (rc == FIO_OK && fio_tc_timeout_reset() > 0) rc = FIO_ETIMEOUT;
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------------------------
+// fio_autotune: per-stage choice of the kernel variant by timing the candidates (see fio.h)
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+// time one launch of variant `var` (best of 3 after one warm-up); < 0 when it does not apply
+template <typename V, bool ADJ>
+float time_variant(const StageArgs<V>& a, cudaStream_t s, int var, cudaEvent_t e0, cudaEvent_t e1) {
+  if (!launch_variant<V, ADJ>(a, s, var)) return -1.f;
+  float best = -1.f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, s);
+    launch_variant<V, ADJ>(a, s, var);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -2.f;
+    if (best < 0.f || ms < best) best = ms;
+  }
+  return best;
+}
+
+// tune every stage launch of one vector type at b right-hand sides; choices[] gets the variant
+// per (stage, direction) in stage order, forward before adjoint
+template <typename V>
+int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch) {
+  void* bufs[5];
+  int rc = fio_scratch(op, b, sizeof(V), s, bufs);
+  if (rc) return rc;
+  const size_t bytes = (size_t)op->max_len * b * sizeof(V);
+  V* X = (V*)bufs[0];
+  V* Y = (V*)bufs[1];
+  if (cudaMemsetAsync(X, 0, bytes, s) != cudaSuccess || cudaMemsetAsync(Y, 0, bytes, s) != cudaSuccess)
+    return FIO_ECUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return FIO_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return FIO_ECUDA;
+  }
+  const int bucket = rhs_bucket(b), ti = type_index<V>();
+  int n = 0;
+  rc = FIO_OK;
+  for (int si = 0; si < (int)op->st.size() && rc == FIO_OK; ++si) {
+    Stage& st = op->st[si];
+    const bool root = si >= op->n_bf + op->n_hif;
+    for (int dir = 0; dir < (root ? 1 : 2) && rc == FIO_OK; ++dir) {
+      const bool adj = dir == 1;
+      int best = 0;
+      if (st.nblk > 0 && !use_tc<V>(st, b)) {
+        const StageArgs<V> a = stage_args<V>(st, adj, X, b, 1, Y, b, 1, b);
+        float tbest = -1.f;
+        for (int k = 0; k < 5 && kCand[bucket][k] > 0; ++k) {
+          const int var = kCand[bucket][k];
+          const float t = adj ? time_variant<V, true>(a, s, var, e0, e1) : time_variant<V, false>(a, s, var, e0, e1);
+          if (t == -2.f || cudaGetLastError() != cudaSuccess) {
+            rc = FIO_ECUDA;
+            break;
+          }
+          if (t >= 0.f && (tbest < 0.f || t < tbest)) {
+            tbest = t;
+            best = var;
+          }
+        }
+      }
+      st.var[ti][dir][bucket] = (int8_t)best;
+      if (choices && n < cap) choices[n] = best;
+      ++n;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (nch) *nch = n;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int fio_autotune(fio_op op, int b, int precision, void* stream, int* choices, int cap, int* nchoices) {
+  if (!op || b < 0 || cap < 0 || (cap > 0 && !choices)) return FIO_EINVAL;
+  if (precision < FIO_P64 || precision > FIO_PDF) return FIO_EINVAL;
+  if (precision == FIO_P64 && !op->arena) return FIO_EINVAL;
+  if ((precision == FIO_P32 || is_tc_precision(precision)) && !op->arena32) return FIO_EINVAL;
+  if (is_tc_precision(precision) && !op->arena_tc) return FIO_EINVAL;
+  if (precision == FIO_PDF && !op->arena_df) return FIO_EINVAL;
+  if (nchoices) *nchoices = 0;
+  if (b == 0) return FIO_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaGetLastError() != cudaSuccess) return FIO_ECUDA;
+  int rc;
+  if (precision == FIO_P64) {
+    rc = tune_type<double2>(op, b, s, choices, cap, nchoices);
+  } else if (precision == FIO_PDF) {
+    rc = tune_type<dfc>(op, b, s, choices, cap, nchoices);
+  } else {
+    TcMode m(tc_mode_of(precision));
+    rc = tune_type<float2>(op, b, s, choices, cap, nchoices);
+  }
+  if (rc == FIO_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = FIO_ECUDA;
   return rc;
 }
 
@@ -812,6 +1028,7 @@ extern "C" int fio_apply_inv_noalloc(fio_op op, const void* u, void* f, int64_t 
                                      int dtype, int precision, void* stream) {
   int rc = check_args(op, u, f, ld, b, dtype, precision);
   if (rc) return rc;
+  if (precision == FIO_PDF) return FIO_EINVAL;  // the static scratch serves P64, P32 and tensor cores
   if (op->n_root == 0) return FIO_ENOTSUP;
   if (b == 0) return FIO_OK;
   const size_t es = precision == FIO_P64 ? sizeof(double2) : sizeof(float2);

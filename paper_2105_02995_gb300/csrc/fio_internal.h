@@ -11,6 +11,8 @@
 
 namespace fio {
 
+struct dfc;  // double-float complex (fio_kernels.cuh)
+
 struct Stage {
   uint32_t kind, nblk, R, C;
   int64_t in_len, out_len;
@@ -18,6 +20,7 @@ struct Stage {
   uint32_t level, role;
   const double2* M64 = nullptr;  // device, complex128 blocks (inside the arena)
   const float2* M32 = nullptr;   // device, complex64 copy (inside arena32)
+  const dfc* Mdf = nullptr;      // device, double-float copy (inside arena_df)
   const int* in = nullptr;       // device
   const int* out = nullptr;      // device
   long long launch_rows;
@@ -36,6 +39,9 @@ struct Stage {
   const int2* t128_fwd = nullptr;
   const int2* t128_adj = nullptr;
   int n128_fwd = 0, n128_adj = 0;
+  // kernel variant chosen by fio_autotune per [vector type: c128, c64, double-float][direction:
+  // forward, adjoint][right-hand-side bucket]; 0 = the built-in choice (see fio_capi.cu)
+  int8_t var[3][2][5] = {};
 };
 
 }  // namespace fio
@@ -55,11 +61,16 @@ struct fio_op_s {
   size_t scratch_bytes = 0;
   void* arena_tc = nullptr;       // tensor-core copies of every stage's blocks
   size_t arena_tc_bytes = 0;
+  void* arena_df = nullptr;       // double-float copies of every stage's blocks
+  size_t arena_df_bytes = 0;
   void* meta = nullptr;           // per-block dims and tile lists of every stage
   size_t meta_bytes = 0;
   void* solver = nullptr;         // solver work arrays (fio_solve.cu)
   size_t solver_bytes = 0;
 };
+
+// precisions whose stage products may run on the tensor cores (complex64 vectors)
+inline bool is_tc_precision(int p) { return p == FIO_PTF32 || p == FIO_PBF16 || p == FIO_PTF32X3; }
 
 // scratch work arrays (5 of max_len x b elements of `elem` bytes); grows with a stream sync
 int fio_scratch(fio_op op, int b, size_t elem, cudaStream_t s, void** bufs);

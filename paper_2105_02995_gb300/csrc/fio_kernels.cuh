@@ -16,9 +16,9 @@
 //               memory (M chunk stored column-chunk-major, the gathered x chunk row-major) and
 //               keeps a TR x TB register tile of complex accumulators per thread.  Each factor
 //               entry is read from HBM once per right-hand-side tile.
-//   k_stage_mv  b <= 4: the factor is used at most 4 times, so the kernel is a streaming matvec:
-//               forward one warp per block row (lanes along the row, coalesced), adjoint one
-//               thread per block column (rows walked in order, coalesced).
+//   k_stage_vec b <= 4: the factor is used at most 4 times, so the kernel streams it once,
+//               coalesced, with the tile's gathered inputs in shared memory (forward: a warp
+//               per row; adjoint: threads along the columns).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,6 +45,94 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 template <typename V> __device__ __forceinline__ V czero();
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+
+// ---- double-float complex: FP64-class accuracy from FP32 arithmetic -------------------------
+// A value is (rh + rl) + i (ih + il) with |rl| <= ulp(rh) / 2 (the "double-float" format of
+// Dekker, 1971: two non-overlapping floats, 48-bit significand).  GB300's FP64 pipes are a small
+// fraction of its FP32 rate, so the FP64-accuracy residual of iterative refinement runs in this
+// format.  Products are accumulated with the compensated dot product of Ogita, Rump and Oishi
+// (2005, "Dot2"): each real product a*b of two double-floats is split exactly into
+// ph + pe (TwoProduct by FMA, plus the cross terms ah*bl + al*bh), ph is added to the running sum
+// s by Knuth's TwoSum (exact error e), and the errors e + pe collect in a compensation c; the
+// result is (s, c) renormalised.  Its error is that of a sum in twice the working precision plus
+// one rounding to double-float.  Arithmetic uses __fmul_rn / __fadd_rn / __fsub_rn so that no
+// multiply is contracted into an FMA, which would break the error-free transformations.
+struct __align__(16) dfc {
+  float rh, ih, rl, il;
+};
+// accumulator in the same four floats: (s_re, s_im, c_re, c_im) until cfin renormalises it
+__device__ __forceinline__ void dot2_step(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float ph = __fmul_rn(ah, bh);
+  float pe = fmaf(ah, bh, -ph);
+  pe = fmaf(ah, bl, pe);
+  pe = fmaf(al, bh, pe);
+  const float t = __fadd_rn(s, ph);
+  const float z = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(ph, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ dfc cmac(dfc acc, dfc a, dfc b) {
+  // re += a.re b.re - a.im b.im ; im += a.re b.im + a.im b.re
+  dot2_step(acc.rh, acc.rl, a.rh, a.rl, b.rh, b.rl);
+  dot2_step(acc.rh, acc.rl, a.ih, a.il, -b.ih, -b.il);
+  dot2_step(acc.ih, acc.il, a.rh, a.rl, b.ih, b.il);
+  dot2_step(acc.ih, acc.il, a.ih, a.il, b.rh, b.rl);
+  return acc;
+}
+__device__ __forceinline__ dfc cconj(dfc a) { return dfc{a.rh, -a.ih, a.rl, -a.il}; }
+template <> __device__ __forceinline__ dfc czero<dfc>() { return dfc{0.f, 0.f, 0.f, 0.f}; }
+// (s, c) -> double-float (hi, lo) with hi = fl(s + c) (Fast2Sum: |c| is below ulp-scale of |s|)
+__device__ __forceinline__ void df_norm(float s, float c, float& hi, float& lo) {
+  hi = __fadd_rn(s, c);
+  lo = __fsub_rn(c, __fsub_rn(hi, s));
+}
+// sum of two accumulators (s1, c1) + (s2, c2): TwoSum of the leading parts, errors to c
+__device__ __forceinline__ void df_acc_add(float& s, float& c, float s2, float c2) {
+  const float t = __fadd_rn(s, s2);
+  const float z = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(c2, e));
+}
+
+// value stored from an accumulator (identity but for the double-float renormalisation)
+__device__ __forceinline__ double2 cfin(double2 v) { return v; }
+__device__ __forceinline__ float2 cfin(float2 v) { return v; }
+__device__ __forceinline__ dfc cfin(dfc v) {
+  dfc o;
+  df_norm(v.rh, v.rl, o.rh, o.rl);
+  df_norm(v.ih, v.il, o.ih, o.il);
+  return o;
+}
+// a += b for accumulators
+__device__ __forceinline__ void cacc_add(double2& a, double2 b) {
+  a.x += b.x;
+  a.y += b.y;
+}
+__device__ __forceinline__ void cacc_add(float2& a, float2 b) {
+  a.x += b.x;
+  a.y += b.y;
+}
+__device__ __forceinline__ void cacc_add(dfc& a, dfc b) {
+  df_acc_add(a.rh, a.rl, b.rh, b.rl);
+  df_acc_add(a.ih, a.il, b.ih, b.il);
+}
+// every member of a value exchanged with lane (lane ^ o)
+__device__ __forceinline__ void shfl_xor_all(double2& v, int o) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+}
+__device__ __forceinline__ void shfl_xor_all(float2& v, int o) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+}
+__device__ __forceinline__ void shfl_xor_all(dfc& v, int o) {
+  v.rh = __shfl_xor_sync(0xffffffffu, v.rh, o);
+  v.ih = __shfl_xor_sync(0xffffffffu, v.ih, o);
+  v.rl = __shfl_xor_sync(0xffffffffu, v.rl, o);
+  v.il = __shfl_xor_sync(0xffffffffu, v.il, o);
+}
 
 template <typename V>
 struct StageArgs {
@@ -164,7 +252,7 @@ __global__ void __launch_bounds__(256) k_stage_mm(StageArgs<V> a) {
 #pragma unroll
     for (int k = 0; k < TB; ++k) {
       const int j = j0 + tx + TX * k;
-      if (j < a.b) a.y[(long long)idx * a.yrs + (long long)j * a.ycs] = acc[i][k];
+      if (j < a.b) a.y[(long long)idx * a.yrs + (long long)j * a.ycs] = cfin(acc[i][k]);
     }
   }
 }
@@ -282,73 +370,131 @@ __global__ void __launch_bounds__(256) k_stage_mm_pipe(StageArgs<V> a) {
 #pragma unroll
     for (int q = 0; q < TB; ++q) {
       const int j = j0 + tx + TX * q;
-      if (j < a.b) a.y[(long long)idx * a.yrs + (long long)j * a.ycs] = acc[i][q];
+      if (j < a.b) a.y[(long long)idx * a.yrs + (long long)j * a.ycs] = cfin(acc[i][q]);
     }
   }
 }
 
-// forward streaming matvec: one warp per block row, b <= 4
-template <typename V>
-__global__ void __launch_bounds__(256) k_stage_mv_fwd(StageArgs<V> a) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const long long total = (long long)a.nblk * a.R;
-  if (warp >= total) return;
-  const int blk = warp / a.R;
-  const int r = warp - blk * a.R;
-  const int Rb = a.dims ? a.dims[blk].x : a.R;
-  const int Cb = a.dims ? a.dims[blk].y : a.C;
-  if (r >= Rb) return;
-  const int oidx = a.out[(size_t)blk * a.R + r];
-  if (oidx < 0) return;
-  const V* Mr = a.M + ((size_t)blk * a.R + r) * a.C;
-  const int* in = a.in + (size_t)blk * a.C;
-  V acc[4] = {czero<V>(), czero<V>(), czero<V>(), czero<V>()};
-  for (int c = lane; c < Cb; c += 32) {
-    const int ic = in[c];
-    if (ic < 0) continue;
-    const V m = Mr[c];
+// ---- few right-hand sides (b <= 4): one CTA per (block, 64-row tile) ------------------------
+// The tile's gathered input rows (ncols x b values) are copied once into shared memory, laid out
+// right-hand-side major (sX[j * ncols + c]) so that consecutive c sit in consecutive slots; the
+// factor is then streamed once, coalesced, with the work split to the block's width (butterfly
+// blocks can be as narrow as one 16-point leaf):
+//   forward  groups of w lanes (w = 4 .. 32, about ncols / 4 rounded up to a power of two) own
+//            one row each and stride along it; the row's sums are reduced within the group;
+//   adjoint  the tile's T output columns (T = 4 .. 64, a power of two >= its valid columns) each
+//            get 256 / T threads that take every (256 / T)-th row; the partial sums are added by
+//            a tree in shared memory.
+// Dynamic shared memory: max(ncols * b, ADJ ? 256 * b : 0) values.
+constexpr int kVecMaxRhs = 4;
+
+// forward rows of k_stage_vec: groups of W lanes, one row per group, B right-hand sides
+template <typename V, int W, int B>
+__device__ __forceinline__ void vec_rows(const StageArgs<V>& a, const V* M, const int* rowidx, const V* sX,
+                                         int r0, int nrows, int ncols) {
+  constexpr int PER_WARP = 32 / W;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = lane & (W - 1);
+  const int nr = min(64, nrows - r0);
+  for (int rb = warp * PER_WARP; rb < nr; rb += 8 * PER_WARP) {  // warp-uniform trip count
+    const int rr = rb + lane / W;
+    const bool live = rr < nr;
+    V acc[B];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < a.b) acc[j] = cmac(acc[j], m, a.x[(long long)ic * a.xrs + (long long)j * a.xcs]);
-  }
+    for (int j = 0; j < B; ++j) acc[j] = czero<V>();
+    if (live) {
+      const V* Mr = M + (size_t)(r0 + rr) * a.C;
+#pragma unroll 4
+      for (int c = sub; c < ncols; c += W) {
+        const V m = Mr[c];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (j >= a.b) break;
-    V v = acc[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        for (int j = 0; j < B; ++j) acc[j] = cmac(acc[j], m, sX[j * ncols + c]);
+      }
     }
-    if (lane == 0) a.y[(long long)oidx * a.yrs + (long long)j * a.ycs] = v;
+    const int oidx = live ? rowidx[r0 + rr] : -1;
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      V v = acc[j];
+#pragma unroll
+      for (int o = W >> 1; o > 0; o >>= 1) {
+        V t = v;
+        shfl_xor_all(t, o);
+        cacc_add(v, t);
+      }
+      if (sub == 0 && oidx >= 0) a.y[(long long)oidx * a.yrs + (long long)j * a.ycs] = cfin(v);
+    }
   }
 }
 
-// adjoint streaming matvec: one thread per block column, b <= 4
-template <typename V>
-__global__ void __launch_bounds__(256) k_stage_mv_adj(StageArgs<V> a) {
-  const int blk = blockIdx.y;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int Rb = a.dims ? a.dims[blk].x : a.R;
-  const int Cb = a.dims ? a.dims[blk].y : a.C;
-  if (c >= Cb) return;
-  const int ic = a.in[(size_t)blk * a.C + c];
-  if (ic < 0) return;
-  const V* M = a.M + (size_t)blk * a.R * a.C + c;
-  const int* out = a.out + (size_t)blk * a.R;
-  V acc[4] = {czero<V>(), czero<V>(), czero<V>(), czero<V>()};
-  for (int r = 0; r < Rb; ++r) {
-    const int orow = out[r];
-    if (orow < 0) continue;
-    const V m = cconj(M[(size_t)r * a.C]);
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < a.b) acc[j] = cmac(acc[j], m, a.x[(long long)orow * a.xrs + (long long)j * a.xcs]);
+// The number of right-hand sides B (1..4) is a template parameter: every accumulator slot is
+// live, so no predicated-off multiply occupies an issue slot (on GB300 an FP64 FMA slot is
+// scarce).
+template <typename V, bool ADJ, int B>
+__global__ void __launch_bounds__(256) k_stage_vec(StageArgs<V> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sX = reinterpret_cast<V*>(smem_raw);
+  int blk, tile, Rb, Cb;
+  cta_work<V, ADJ>(a, blk, tile, Rb, Cb);
+  const int nrows = ADJ ? Cb : Rb;
+  const int ncols = ADJ ? Rb : Cb;
+  const V* M = a.M + (size_t)blk * a.R * a.C;
+  const int* rowidx = ADJ ? a.in + (size_t)blk * a.C : a.out + (size_t)blk * a.R;
+  const int* colidx = ADJ ? a.out + (size_t)blk * a.R : a.in + (size_t)blk * a.C;
+  const int r0 = tile * 64;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < ncols * B; e += 256) {
+    const int j = e / ncols, c = e - j * ncols;
+    const int idx = colidx[c];
+    sX[e] = idx >= 0 ? a.x[(long long)idx * a.xrs + (long long)j * a.xcs] : czero<V>();
   }
+  __syncthreads();
+  if (!ADJ) {
+    int w = 4;
+    while (w < 32 && 4 * w < ncols) w <<= 1;
+    switch (w) {  // uniform per CTA; a compile-time group width keeps the row loop unrolled
+      case 4: vec_rows<V, 4, B>(a, M, rowidx, sX, r0, nrows, ncols); break;
+      case 8: vec_rows<V, 8, B>(a, M, rowidx, sX, r0, nrows, ncols); break;
+      case 16: vec_rows<V, 16, B>(a, M, rowidx, sX, r0, nrows, ncols); break;
+      default: vec_rows<V, 32, B>(a, M, rowidx, sX, r0, nrows, ncols); break;
+    }
+  } else {
+    const int nc = min(64, nrows - r0);
+    int T = 4;
+    while (T < nc) T <<= 1;
+    const int G = 256 / T;
+    const int cl = tid & (T - 1), g = tid / T, c = r0 + cl;
+    V acc[B];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if (j < a.b) a.y[(long long)ic * a.yrs + (long long)j * a.ycs] = acc[j];
+    for (int j = 0; j < B; ++j) acc[j] = czero<V>();
+    if (cl < nc) {
+      for (int r = g; r < ncols; r += G) {
+        const V m = cconj(M[(size_t)r * a.C + c]);
+#pragma unroll
+        for (int j = 0; j < B; ++j) acc[j] = cmac(acc[j], m, sX[j * ncols + r]);
+      }
+    }
+    __syncthreads();  // every thread is done with sX: reuse it for the partial sums
+#pragma unroll
+    for (int j = 0; j < B; ++j) sX[j * 256 + tid] = acc[j];
+    for (int h = G >> 1; h > 0; h >>= 1) {
+      __syncthreads();
+      if (g < h) {
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+          V v = sX[j * 256 + tid];
+          cacc_add(v, sX[j * 256 + tid + h * T]);
+          sX[j * 256 + tid] = v;
+        }
+      }
+    }
+    __syncthreads();
+    if (g == 0 && cl < nc) {
+      const int oidx = rowidx[c];
+      if (oidx >= 0) {
+#pragma unroll
+        for (int j = 0; j < B; ++j) a.y[(long long)oidx * a.yrs + (long long)j * a.ycs] = cfin(sX[j * 256 + tid]);
+      }
+    }
+  }
 }
 
 // INPLACE stages compute into a scratch vector S (same row numbering) and then copy the touched
@@ -405,6 +551,30 @@ __global__ void k_row_to_col(const V* W, V* Y, long long ld, long long N, int b)
 __global__ void k_cast_c128_c64(const double2* a, float2* b, size_t n) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) b[t] = make_float2((float)a[t].x, (float)a[t].y);
+}
+
+// complex128 -> double-float: hi = fl32(v), lo = fl32(v - hi) (v - hi is exact in FP64)
+__device__ __forceinline__ dfc split_df(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return dfc{rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih)};
+}
+__global__ void k_split_df(const double2* a, dfc* b, size_t n) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = split_df(a[t]);
+}
+// N x b column-major complex128 (leading dimension ld) -> double-float (leading dimension N), and back
+__global__ void k_c128_to_df(const double2* x, long long ld, dfc* y, long long N, int b) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * b) return;
+  const long long j = t / N, i = t - j * N;
+  y[t] = split_df(x[j * ld + i]);
+}
+__global__ void k_df_to_c128(const dfc* y, long long N, double2* x, long long ld, int b) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * b) return;
+  const long long j = t / N, i = t - j * N;
+  const dfc v = y[t];
+  x[j * ld + i] = make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
 }
 
 }  // namespace fio

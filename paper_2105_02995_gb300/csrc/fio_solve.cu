@@ -7,8 +7,9 @@
 //          extra apply.
 //   GMRES  restarted GMRES on K-dot f = u right-preconditioned with P = G-dot K-dot*; classical
 //          Gram-Schmidt applied twice, Givens rotations per right-hand side on the host.
-//   IR     iterative refinement: r = u - K-dot f in FP64, d = G-dot K-dot* r in the inner
-//          precision (FP32 or FP64 factors), f += d in FP64.
+//   IR     iterative refinement: r = u - K-dot f on FP64 vectors (FP64 or double-float stage
+//          arithmetic), d = G-dot K-dot* r in the inner precision (FP64, FP32 or tensor-core
+//          factors), f += d in FP64.
 // Every right-hand side has its own scalars; all of them advance together, a converged one is
 // frozen.  Reductions are FP64 and in a fixed order (one CTA per column, fixed tree), so the
 // results do not depend on scheduling.
@@ -171,7 +172,9 @@ struct Ctx {
   long long N;
   int b;
   cudaStream_t s;
-  double2* dsc;  // device scalar scratch (4 x b)
+  double2* dsc;         // device scalar scratch (4 x b)
+  int outer = FIO_P64;  // precision of the true residuals (FIO_P64 or FIO_PDF)
+  bool f_zero = false;  // f is known to be zero (the next residual is u itself)
 };
 
 int dots(Ctx& c, const double2* a, long long lda, const double2* bb, long long ldb, double2* out_dev,
@@ -209,16 +212,24 @@ int precond(Ctx& c, Work& w, int which, const double2* x, double2* y, int prec) 
   if (prec == FIO_P64) return fio_apply_internal(c.op, which, x, y, c.N, c.b, FIO_P64, c.s);
   const long long n = c.N * c.b;
   k_to32<<<nblocks(n), 256, 0, c.s>>>(x, w.v32[0], n);
-  int rc = fio_apply_internal(c.op, which, w.v32[0], w.v32[1], c.N, c.b, FIO_P32, c.s);
+  int rc = fio_apply_internal(c.op, which, w.v32[0], w.v32[1], c.N, c.b, prec, c.s);
   if (rc) return rc;
   cudaMemsetAsync(y, 0, n * sizeof(double2), c.s);
   k_add32<<<nblocks(n), 256, 0, c.s>>>(w.v32[1], y, c.N, c.N, c.b);
   return cudaGetLastError() == cudaSuccess ? FIO_OK : FIO_ECUDA;
 }
 
-// s = u - K-dot f   (s, tmp: ld N; u, f: ld)
+// s = u - K-dot f   (s, tmp: ld N; u, f: ld), K-dot in the outer precision; when f is known to
+// be zero, s = u without an apply
 int residual(Ctx& c, const double2* u, long long ld, const double2* f, double2* s) {
-  int rc = fio_apply_internal(c.op, 0, f, s, ld, c.b, FIO_P64, c.s);
+  if (c.f_zero) {
+    c.f_zero = false;
+    return cudaMemcpy2DAsync(s, c.N * sizeof(double2), u, ld * sizeof(double2), c.N * sizeof(double2), c.b,
+                             cudaMemcpyDeviceToDevice, c.s) == cudaSuccess
+               ? FIO_OK
+               : FIO_ECUDA;
+  }
+  int rc = fio_apply_internal(c.op, 0, f, s, ld, c.b, c.outer, c.s);
   if (rc) return rc;
   std::vector<double2> one(c.b, make_double2(1, 0)), mone(c.b, make_double2(-1, 0));
   // s holds K f with ld = ld; bring it to ld N: s = u - s
@@ -241,9 +252,11 @@ extern "C" int fio_solve(fio_op op, const void* uv, void* fv, int64_t ld, int b,
   if (!op || !opts || b < 0 || dtype != FIO_C128 || ld != op->N) return FIO_EINVAL;
   if (b > 0 && (!uv || !fv || uv == fv)) return FIO_EINVAL;
   if (opts->method < FIO_DIRECT || opts->method > FIO_IR) return FIO_EINVAL;
-  if (opts->inner < FIO_P64 || opts->inner > FIO_PBF16) return FIO_EINVAL;
+  if (opts->inner < FIO_P64 || opts->inner > FIO_PTF32X3) return FIO_EINVAL;
   if (opts->inner != FIO_P64 && !op->arena32) return FIO_EINVAL;
-  if ((opts->inner == FIO_PTF32 || opts->inner == FIO_PBF16) && !op->arena_tc) return FIO_EINVAL;
+  if (is_tc_precision(opts->inner) && !op->arena_tc) return FIO_EINVAL;
+  if (opts->outer != FIO_P64 && opts->outer != FIO_PDF) return FIO_EINVAL;
+  if (opts->outer == FIO_PDF && !op->arena_df) return FIO_EINVAL;
   if (op->n_root == 0) return FIO_ENOTSUP;
   if (b == 0) return FIO_OK;
   const int maxit = opts->maxit > 0 ? opts->maxit : 100;
@@ -253,6 +266,7 @@ extern "C" int fio_solve(fio_op op, const void* uv, void* fv, int64_t ld, int b,
   int rc = get_work(op, b, restart, &w);
   if (rc) return rc;
   Ctx c{op, op->N, b, s, w.sc};
+  c.outer = opts->outer;
   const double2* u = (const double2*)uv;
   double2* f = (double2*)fv;
   const long long N = op->N;
@@ -261,6 +275,12 @@ extern "C" int fio_solve(fio_op op, const void* uv, void* fv, int64_t ld, int b,
   if (rc) return rc;
   std::vector<double> unorm(b);
   for (int j = 0; j < b; ++j) unorm[j] = sqrt(tmp[j].x) > 0 ? sqrt(tmp[j].x) : 1.0;
+  if (opts->method != FIO_DIRECT) {  // a zero initial guess needs no apply for its residual
+    rc = dots(c, f, N, f, N, w.sc + 2 * b, &tmp);
+    if (rc) return rc;
+    c.f_zero = true;
+    for (int j = 0; j < b; ++j) c.f_zero = c.f_zero && tmp[j].x == 0.0;
+  }
   std::vector<double> relres(b, 1.0);
   std::vector<int> iters(b, 0);
   std::vector<char> done(b, 0);

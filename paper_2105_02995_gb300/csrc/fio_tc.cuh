@@ -21,6 +21,13 @@
 // per CTA keeps shared memory near 30 KB so that six to seven CTAs share an SM and overlap one
 // another's copies and MMAs; measured faster than two or three buffers per CTA at fewer CTAs.
 // Tensor memory is allocated by warp 0 and freed on every path.
+//
+// Split-TF32 mode (kTcX3): FP32-accurate products on the TF32 tensor cores.  Every operand value
+// v is split as v = hi + lo with hi = round-to-nearest TF32(v) and lo = TF32(v - hi) (v - hi is
+// exact in FP32); the chunk's product is accumulated as A_hi B_hi + A_hi B_lo + A_lo B_hi (twelve
+// MMAs per chunk instead of four), dropping only A_lo B_lo, of relative size 2^-22.  The A tile
+// is split in shared memory after it lands (hi written back in place, lo into a second tile), so
+// the HBM traffic is that of the TF32 mode; B is split while it is expanded.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -90,6 +97,13 @@ __host__ __device__ constexpr uint32_t idesc(uint32_t ab_fmt, int M, int N) {
   return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// round to the nearest TF32 value (ties away from zero), returned in FP32 format
+__device__ __forceinline__ float tf32_rna(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
 template <bool BF16>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
   if (BF16)
@@ -130,7 +144,7 @@ __device__ __forceinline__ uint32_t swz(int row, int chunk) {
 }  // namespace tc
 
 struct TcArgs {
-  const void* A;      // op-matrix blocks: float2 (TF32) or __nv_bfloat162 (BF16), row-major
+  const void* A;      // op-matrix blocks: float2 (TF32, split TF32) or __nv_bfloat162 (BF16), row-major
   long long bstride;  // elements between blocks
   int lda;            // elements between rows
   const int* rowidx;  // output index list base (out for forward, in for adjoint), per block stride
@@ -150,28 +164,36 @@ struct TcArgs {
 
 constexpr int kTcRows = 128;
 constexpr int kTcMaxRhs = 64;  // right-hand sides per CTA (N = 128 accumulator columns)
-// dynamic shared memory: A tile (16 KB) + B tile (N x 128 B) + staging of the chunk's x rows
-// (KC rows x N/2 complex) + alignment slack, for accumulator width N (= 2 x right-hand sides)
-// + the block's gather list (ncmax int32)
-__host__ __device__ constexpr int tc_smem_bytes(bool bf16, int N, int ncmax) {
-  return 16384 + N * 128 + (bf16 ? 32 : 16) * (N / 2) * 8 + 1024 + ((ncmax + 3) & ~3) * 4;
+// operand modes of k_stage_tc
+constexpr int kTcTF32 = 1, kTcBF16 = 2, kTcX3 = 3;
+// dynamic shared memory: A tile (16 KB) + B tile (N x 128 B) (both twice in split-TF32 mode) +
+// staging of the chunk's x rows (KC rows x N/2 complex) + alignment slack, for accumulator width
+// N (= 2 x right-hand sides) + the block's gather list (ncmax int32)
+__host__ __device__ constexpr int tc_smem_bytes(int mode, int N, int ncmax) {
+  return (mode == kTcX3 ? 2 : 1) * (16384 + N * 128) + (mode == kTcBF16 ? 32 : 16) * (N / 2) * 8 + 1024 +
+         ((ncmax + 3) & ~3) * 4;
 }
 
-template <bool ADJ, bool BF16>
+template <bool ADJ, int MODE>
 __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
   using namespace tc;
+  constexpr bool BF16 = MODE == kTcBF16;
+  constexpr bool X3 = MODE == kTcX3;
+  constexpr uint32_t TA = X3 ? 32768u : 16384u;  // bytes of the A tile(s)
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
   extern __shared__ __align__(16) uint8_t smem_dyn[];
-  // layout: A tile (16 KB, 1024-byte aligned for the swizzle atoms), B tile (N x 128 B), x staging
-  // (KC rows x nmax/2 complex)
+  // layout: A tile (16 KB, 1024-byte aligned for the swizzle atoms; split mode: A_hi then A_lo),
+  // B tile (N x 128 B; split mode: B_hi then B_lo), x staging (KC rows x nmax/2 complex), gather list
   const uint32_t base = (su32(smem_dyn) + 1023u) & ~1023u;
   uint8_t* gbase = smem_dyn + (base - su32(smem_dyn));
-  const uint32_t sA = base, sB = base + 16384;
-  uint8_t* pB = gbase + 16384;
-  const uint32_t sX = sB + (uint32_t)a.nmax * 128;
-  const float2* pX = reinterpret_cast<const float2*>(gbase + 16384 + a.nmax * 128);
-  int* sIdx = reinterpret_cast<int*>(gbase + 16384 + a.nmax * 128 + (BF16 ? 32 : 16) * (a.nmax / 2) * 8);
+  const uint32_t TB = (uint32_t)a.nmax * 128;  // bytes of one B tile (a multiple of 2048)
+  const uint32_t sA = base, sB = base + TA;
+  uint8_t* pA = gbase;
+  uint8_t* pB = gbase + TA;
+  const uint32_t sX = sB + (X3 ? 2 : 1) * TB;
+  const float2* pX = reinterpret_cast<const float2*>(gbase + TA + (X3 ? 2 : 1) * TB);
+  int* sIdx = reinterpret_cast<int*>(gbase + TA + (X3 ? 2 : 1) * TB + (BF16 ? 32 : 16) * (a.nmax / 2) * 8);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int2 t = a.tiles[blockIdx.x];
@@ -257,10 +279,30 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
         const int ch = c >> 2, off = (c & 3) << 2;
         *reinterpret_cast<__nv_bfloat162*>(pB + swz(n0, ch) + off) = __floats2bfloat162_rn(p0, p1);
         *reinterpret_cast<__nv_bfloat162*>(pB + swz(n1, ch) + off) = __floats2bfloat162_rn(q0, q1);
+      } else if (X3) {
+        const int ch = c >> 1, off = (c & 1) << 3;
+        const float hp0 = tf32_rna(p0), hp1 = tf32_rna(p1), hq0 = tf32_rna(q0), hq1 = tf32_rna(q1);
+        *reinterpret_cast<float2*>(pB + swz(n0, ch) + off) = make_float2(hp0, hp1);
+        *reinterpret_cast<float2*>(pB + swz(n1, ch) + off) = make_float2(hq0, hq1);
+        *reinterpret_cast<float2*>(pB + TB + swz(n0, ch) + off) =
+            make_float2(tf32_rna(p0 - hp0), tf32_rna(p1 - hp1));
+        *reinterpret_cast<float2*>(pB + TB + swz(n1, ch) + off) =
+            make_float2(tf32_rna(q0 - hq0), tf32_rna(q1 - hq1));
       } else {
         const int ch = c >> 1, off = (c & 1) << 3;
         *reinterpret_cast<float2*>(pB + swz(n0, ch) + off) = make_float2(p0, p1);
         *reinterpret_cast<float2*>(pB + swz(n1, ch) + off) = make_float2(q0, q1);
+      }
+    }
+    if (X3) {
+      // split the A tile in place: the split is elementwise, so A_lo takes the same swizzled layout
+      for (int e = tid; e < kTcRows * 8; e += 128) {
+        float4* h = reinterpret_cast<float4*>(pA + 16 * e);
+        const float4 v = *h;
+        const float4 hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+        *h = hi;
+        *reinterpret_cast<float4*>(pA + 16384 + 16 * e) =
+            make_float4(tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z), tf32_rna(v.w - hi.w));
       }
     }
     fence_async_smem();
@@ -269,8 +311,16 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
     if (tid == 0) {
       fence_after();
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        mma<BF16>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
+      for (int q = 0; q < 4; ++q) {
+        if (X3) {
+          // small terms first: A_lo B_hi, A_hi B_lo, then A_hi B_hi
+          mma<false>(tmem, sdesc(sA + 16384 + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
+          mma<false>(tmem, sdesc(sA + 32 * q), sdesc(sB + TB + 32 * q), id, 1u);
+          mma<false>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, 1u);
+        } else {
+          mma<BF16>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
+        }
+      }
       mma_commit(&s_bar);
     }
   }

@@ -199,11 +199,12 @@ def main(argv=None):
     ap.add_argument("--mix", default="ex1:4096:1e-7:1e-6,ex1:16384:1e-7:1e-6,ex3:64:1e-4:1e-3,ex3:128:1e-4:1e-3")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--load", type=float, default=0.7, help="offered load as a fraction of capacity")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "tf32x3"])
     ap.add_argument("--seed", type=int, default=2105_02995 + 4000)
     a = ap.parse_args(argv)
     fbuild.build()
-    prec = {"fp32": binding.FIO_P32, "tf32": binding.FIO_PTF32, "bf16": binding.FIO_PBF16}[a.precision]
+    prec = {"fp32": binding.FIO_P32, "tf32": binding.FIO_PTF32, "bf16": binding.FIO_PBF16,
+            "tf32x3": binding.FIO_PTF32X3}[a.precision]
     ops = {}
     for spec in a.mix.split(","):
         kind, n, eb, eh = spec.split(":")

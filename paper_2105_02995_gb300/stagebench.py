@@ -51,7 +51,8 @@ def main(argv=None):
     for i in range(nblk * R // 16):
         s2.add(eye, np.arange(16 * i, 16 * i + 16), np.arange(16 * i, 16 * i + 16))
     op = binding.Operator(pack(1, N, [s1, s2], [], [], 0.0, 0.0))
-    precs = {"fp32": binding.FIO_P32, "tf32": binding.FIO_PTF32, "bf16": binding.FIO_PBF16}
+    precs = {"fp32": binding.FIO_P32, "tf32": binding.FIO_PTF32, "bf16": binding.FIO_PBF16,
+             "tf32x3": binding.FIO_PTF32X3}
     out = {"nblk": nblk, "rows": R, "cols": C}
     for b in [int(v) for v in a.b.split(",")]:
         x = binding.colmajor(torch.randn(N, b, dtype=torch.complex64, device="cuda"))

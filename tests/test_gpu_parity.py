@@ -152,32 +152,66 @@ def test_iterative_solves(method, inner):
 # Tensor-core precisions (tcgen05): operands rounded to TF32 (unit roundoff 2^-11) or bfloat16
 # (2^-8) before products accumulated in FP32.  Per stage ~sqrt(2) u relative, over up to ~15
 # stages in a row: TF32 ~ 3e-3, BF16 ~ 2e-2; the bounds below leave a factor ~3.
-TOL_TC = {binding.FIO_PTF32: 1e-2, binding.FIO_PBF16: 5e-2}
+# Split TF32 (head + tail of each operand, three products): each product a*b carries at most
+# 3 * 2^-22 ~ 7e-7 relative (the two rounded tails and the dropped tail*tail), uncorrelated
+# across the terms of a sum, on top of the FP32 accumulation and the FP32 rounding of every
+# stage output that the FP32 path has: ~(1 + 7e-7 / 6e-8 / sqrt(300)) ~ 1.7 times TOL32's
+# derivation, bound 2.5 * TOL32.
+TOL_TC = {binding.FIO_PTF32: 1e-2, binding.FIO_PBF16: 5e-2, binding.FIO_PTF32X3: 2.5 * TOL32}
+TC_PRECS = [binding.FIO_PTF32, binding.FIO_PBF16, binding.FIO_PTF32X3]
+
+
+def _tc_apply(op, fn, xd, b, prec):
+    import ctypes
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    y = binding.colmajor(torch.empty_like(xd))
+    rc = fn(op.h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(y.data_ptr()), xd.shape[0], b,
+            binding.FIO_C64, prec, stream)
+    torch.cuda.synchronize()
+    return rc, y
 
 
 @pytest.mark.parametrize("name", ["ex1_256", "ex3_32"])
-@pytest.mark.parametrize("prec", [binding.FIO_PTF32, binding.FIO_PBF16])
+@pytest.mark.parametrize("prec", TC_PRECS)
 @pytest.mark.parametrize("b", [8, 32, 40, 72])
 def test_apply_tensor_core_vs_factor_oracle(name, prec, b):
-    import ctypes
     buf, info, P, op, ofo = get(name)
     lib = binding.load()
     x = complex_gaussian(ofo.N, b, rhs_seed(0, 300 + b))
     xd = dev(x, torch.complex64)
     x64 = x.astype(np.complex64).astype(np.complex128)
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     for what, fn, ref in (("K", lib.fio_apply_K, fa.apply_Kdot), ("Kadj", lib.fio_apply_Kadj, fa.apply_Kdot_adj),
                           ("inv", lib.fio_apply_inv, fa.apply_inv)):
-        y = binding.colmajor(torch.empty_like(xd))
-        rc = fn(op.h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(y.data_ptr()), ofo.N, b,
-                binding.FIO_C64, prec, stream)
+        rc, y = _tc_apply(op, fn, xd, b, prec)
         assert rc == 0, (what, rc)
-        torch.cuda.synchronize()
         err = rel(host(y), ref(P, x64))
         assert err < TOL_TC[prec], (what, err)
 
 
-@pytest.mark.parametrize("prec", [binding.FIO_PTF32, binding.FIO_PBF16])
+@pytest.mark.parametrize("name", ["ex1_256", "ex3_32"])
+def test_split_tf32_removes_tf32_rounding(name):
+    """The split products are two orders of magnitude closer to the oracle than plain TF32 (a
+    kernel that dropped the tail products would land at the TF32 error), and of the FP32 path's
+    order: the tensor core's FP32 accumulator is not rounded to nearest at every addition, and the
+    split mode adds 3 C / 8 MMA results into it per stage product (C <= ~300 columns), so its
+    error may exceed the FP32 CUDA-core path's (round-to-nearest FMA chains) by about an order
+    of magnitude, bounded here by 20 times."""
+    buf, info, P, op, ofo = get(name)
+    lib = binding.load()
+    b = 32
+    x = complex_gaussian(ofo.N, b, rhs_seed(0, 400))
+    xd = dev(x, torch.complex64)
+    want = fa.apply_Kdot(P, x.astype(np.complex64).astype(np.complex128))
+    errs = {}
+    for prec in (binding.FIO_PTF32, binding.FIO_PTF32X3, binding.FIO_P32):
+        rc, y = _tc_apply(op, lib.fio_apply_K, xd, b, prec)
+        assert rc == 0
+        errs[prec] = rel(host(y), want)
+    assert errs[binding.FIO_PTF32X3] < errs[binding.FIO_PTF32] / 100, errs
+    assert errs[binding.FIO_PTF32X3] < 20 * errs[binding.FIO_P32], errs
+
+
+@pytest.mark.parametrize("prec", TC_PRECS)
 def test_refinement_with_tensor_core_inner(prec):
     """FP64 iterative refinement whose correction G-dot K-dot* r runs on the tensor cores still
     reaches 1e-10 (the outer FP64 residual removes the inner rounding)."""
@@ -190,3 +224,110 @@ def test_refinement_with_tensor_core_inner(prec):
     for j, (it, rr, st) in enumerate(infos):
         assert st == 0 and rr <= 1e-10, infos
         assert np.linalg.norm(u[:, j] - Kd @ fh[:, j]) / np.linalg.norm(u[:, j]) < 3e-10
+
+
+# Double-float (FIO_PDF): every factor entry and vector value as hi + lo floats (48-bit
+# significand, unit roundoff 2^-49 ~ 1.8e-15) with compensated accumulation (sums as if in twice
+# the working precision): per stage a few units of 2^-48 relative, over ~20 stages and sums of
+# ~300 terms well inside TOL64 = 1e-12, the bound of the FP64 path.  A kernel that lost the low
+# parts anywhere would land at the FP32 error (~1e-7).
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("b", [1, 3, 8, 37])
+def test_apply_double_float_vs_factor_oracle(name, b):
+    buf, info, P, op, ofo = get(name)
+    x = complex_gaussian(ofo.N, b, rhs_seed(0, 500 + b))
+    xd = dev(x)
+    for what, ref in (("K", fa.apply_Kdot), ("Kadj", fa.apply_Kdot_adj), ("G", fa.apply_G),
+                      ("inv", fa.apply_inv)):
+        y = getattr(op, "apply_" + what)(xd, precision=binding.FIO_PDF)
+        torch.cuda.synchronize()
+        assert rel(host(y), ref(P, x)) < TOL64, what
+
+
+def test_double_float_precision_pairs():
+    """FIO_PDF takes complex128 vectors only, and the no-allocation entry refuses it."""
+    import ctypes
+    buf, info, P, op, ofo = get("ex1_256")
+    lib = binding.load()
+    x = dev(complex_gaussian(ofo.N, 2, 1), torch.complex64)
+    y = binding.colmajor(torch.empty_like(x))
+    assert lib.fio_apply_K(op.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                           ofo.N, 2, binding.FIO_C64, binding.FIO_PDF, None) == -1
+    x2 = dev(complex_gaussian(ofo.N, 2, 1))
+    y2 = binding.colmajor(torch.empty_like(x2))
+    assert lib.fio_apply_inv_noalloc(op.h, ctypes.c_void_p(x2.data_ptr()), ctypes.c_void_p(y2.data_ptr()),
+                                     ofo.N, 2, binding.FIO_C128, binding.FIO_PDF, None) == -1
+
+
+@pytest.mark.parametrize("inner", [binding.FIO_P32, binding.FIO_PTF32X3])
+def test_refinement_with_double_float_residual(inner):
+    """Iterative refinement whose residuals u - K-dot f are taken in double-float arithmetic
+    reaches 1e-10 against the oracle's dense K-dot (FP64), as with FP64 residuals."""
+    buf, info, P, op, ofo = get("ex1_256")
+    u = complex_gaussian(ofo.N, 8, rhs_seed(2, 1))
+    f, infos = op.solve(dev(u), method=binding.FIO_IR, inner=inner, tol=1e-10, maxit=60,
+                        outer=binding.FIO_PDF)
+    torch.cuda.synchronize()
+    Kd = fa.dense_Kdot(P)
+    fh = host(f)
+    for j, (it, rr, st) in enumerate(infos):
+        assert st == 0 and rr <= 1e-10, infos
+        assert np.linalg.norm(u[:, j] - Kd @ fh[:, j]) / np.linalg.norm(u[:, j]) < 3e-10
+
+
+@pytest.mark.parametrize("method", [binding.FIO_PCG, binding.FIO_GMRES, binding.FIO_IR])
+def test_exact_initial_guess_needs_no_iteration(method):
+    """An initial guess that already solves K-dot f = u (dense solve of the oracle's K-dot) stops
+    at iteration 0: the guess is used, not mistaken for the zero guess whose residual is u."""
+    buf, info, P, op, ofo = get("ex1_256")
+    Kd = fa.dense_Kdot(P)
+    u = complex_gaussian(ofo.N, 3, rhs_seed(2, 2))
+    f0 = dev(np.linalg.solve(Kd, u))
+    f, infos = op.solve(dev(u), f0.clone(), method=method, inner=binding.FIO_P64, tol=1e-10, maxit=50)
+    torch.cuda.synchronize()
+    for it, rr, st in infos:
+        assert st == 0 and it == 0 and rr <= 1e-10, infos
+
+
+# Autotuner: every tile-shape variant sums each output's terms in the same order, so for b >= 5
+# the tuned applies must reproduce the built-in ones bit for bit; for b <= 4 the few-RHS kernel
+# (tree reductions) may be chosen, within the parity tolerances above.
+ALLOWED = {0: {0, 8, 1}, 1: {0, 1, 2}, 2: {0, 2, 3, 4}, 3: {0, 3, 5, 6}, 4: {0, 3, 5, 6, 7}}
+
+
+def _bucket(b):
+    return 0 if b <= 4 else 1 if b <= 8 else 2 if b <= 16 else 3 if b <= 32 else 4
+
+
+@pytest.mark.parametrize("name", ["ex1_1024", "ex3_32"])
+@pytest.mark.parametrize("prec,dt,tol", [(binding.FIO_P64, torch.complex128, TOL64),
+                                         (binding.FIO_P32, torch.complex64, TOL32),
+                                         (binding.FIO_PDF, torch.complex128, TOL64)])
+@pytest.mark.parametrize("b", [2, 16, 37])
+def test_autotune_choices_and_results(name, prec, dt, tol, b):
+    buf, info, P, op, ofo = get(name)
+    x = complex_gaussian(ofo.N, b, rhs_seed(0, 600 + b))
+    xd = dev(x, dt)
+    before = {w: getattr(op, "apply_" + w)(xd, precision=prec).clone() for w in ("K", "Kadj", "inv")}
+    choices = op.autotune(b, prec)
+    assert len(choices) == 2 * (P.n_bf + P.n_hif) + P.n_root
+    assert set(choices) <= ALLOWED[_bucket(b)], choices
+    x64 = x.astype(np.complex64).astype(np.complex128) if dt == torch.complex64 else x
+    for w, ref in (("K", fa.apply_Kdot), ("Kadj", fa.apply_Kdot_adj), ("inv", fa.apply_inv)):
+        after = getattr(op, "apply_" + w)(xd, precision=prec)
+        torch.cuda.synchronize()
+        if b >= 5:
+            assert torch.equal(after, before[w]), w
+        assert rel(host(after), ref(P, x64)) < tol, w
+
+
+def test_autotune_rejects_bad_arguments():
+    import ctypes
+    buf, info, P, op, ofo = get("ex3_32")
+    lib = binding.load()
+    n = ctypes.c_int()
+    assert lib.fio_autotune(None, 4, binding.FIO_P64, None, None, 0, ctypes.byref(n)) == -1
+    assert lib.fio_autotune(op.h, -1, binding.FIO_P64, None, None, 0, ctypes.byref(n)) == -1
+    assert lib.fio_autotune(op.h, 4, 9, None, None, 0, ctypes.byref(n)) == -1
+    assert lib.fio_autotune(op.h, 4, binding.FIO_P64, None, None, 5, ctypes.byref(n)) == -1  # cap > 0, no array
+    assert lib.fio_autotune(op.h, 0, binding.FIO_P64, None, None, 0, ctypes.byref(n)) == 0 and n.value == 0
