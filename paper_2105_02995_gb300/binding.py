@@ -26,7 +26,8 @@ STATUS = {0: "FIO_OK", -1: "FIO_EINVAL", -2: "FIO_ENOMEM", -3: "FIO_EBADFACTORS"
           -4: "FIO_ENOCONV", -5: "FIO_ETIMEOUT", -6: "FIO_ECUDA", -7: "FIO_ENOTSUP"}
 SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv",
            "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_apply_profiled",
-           "fio_apply_inv_noalloc", "fio_selftest_wait", "fio_autotune", "fio_release", "fio_strerror"]
+           "fio_apply_inv_noalloc", "fio_selftest_wait", "fio_autotune", "fio_set_variant", "fio_release",
+           "fio_strerror"]
 
 _lib = None
 
@@ -68,6 +69,7 @@ def load(path: str = LIB_PATH):
                                        ctypes.POINTER(ctypes.c_float), c_int, ctypes.POINTER(c_int)]
     lib.fio_selftest_wait.argtypes = [c_int, c_int, ctypes.POINTER(c_int), vp]
     lib.fio_autotune.argtypes = [vp, c_int, c_int, vp, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int)]
+    lib.fio_set_variant.argtypes = [vp, c_int, c_int, c_int]
     lib.fio_release.argtypes = [vp]
     lib.fio_strerror.argtypes = [c_int]
     lib.fio_strerror.restype = ctypes.c_char_p
@@ -142,6 +144,10 @@ class Operator:
         n = ctypes.c_int()
         _check(self._lib.fio_autotune(self.h, b, precision, _stream(), ch, cap, ctypes.byref(n)), "fio_autotune")
         return [ch[i] for i in range(min(n.value, cap))]
+
+    def set_variant(self, b: int, precision: int, variant: int):
+        """Pin every stage launch of (precision, bucket of b) to one kernel variant (fio_set_variant)."""
+        _check(self._lib.fio_set_variant(self.h, b, precision, variant), "fio_set_variant")
 
     def launches(self, which: str, b: int) -> int:
         k = {"K": 0, "Kadj": 1, "G": 2, "inv": 3}[which]

@@ -531,8 +531,40 @@ void launch_tc_dir(const TcArgs& a, int ncta, cudaStream_t s) {
   k_stage_tc<ADJ, MODE><<<grid, 128, need, s>>>(a);
 }
 
-void launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long long xcs, float2* y,
-               long long yrs, long long ycs, int b, cudaStream_t s) {
+// the ring variant with S stages; false when its shared memory does not fit
+template <bool ADJ, int MODE, int S>
+bool launch_tc_ring(const TcArgs& a, int ncta, cudaStream_t s) {
+  static int cap = 48 * 1024;
+  const int need = tc_ring_smem_bytes(MODE, a.nmax, a.ncmax, S);
+  if (need > 227 * 1024) return false;
+  if (need > cap) {
+    if (cudaFuncSetAttribute(k_stage_tc_ring<ADJ, MODE, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, need) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cap = need;
+  }
+  dim3 grid((unsigned)ncta, (unsigned)((a.b + kTcMaxRhs - 1) / kTcMaxRhs));
+  k_stage_tc_ring<ADJ, MODE, S><<<grid, 192, need, s>>>(a);
+  return true;
+}
+
+// tensor-core variants: 0 the single-buffer kernel, 10 + (S - 2) the ring kernel with S stages
+template <bool ADJ, int MODE>
+bool launch_tc_var(const TcArgs& a, int ncta, cudaStream_t s, int var) {
+  switch (var) {
+    case 0: launch_tc_dir<ADJ, MODE>(a, ncta, s); return true;
+    case 10: return launch_tc_ring<ADJ, MODE, 2>(a, ncta, s);
+    case 11: return launch_tc_ring<ADJ, MODE, 3>(a, ncta, s);
+    case 12: return launch_tc_ring<ADJ, MODE, 4>(a, ncta, s);
+    default: return false;
+  }
+}
+
+// false when variant `var` does not apply (the caller then uses variant 0)
+bool launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long long xcs, float2* y,
+               long long yrs, long long ycs, int b, cudaStream_t s, int var) {
   const bool bf = g_tc_mode == kTcBF16;
   TcArgs a;
   if (!adj) {
@@ -561,14 +593,14 @@ void launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long l
   a.nmax = 2 * ((std::min(b, kTcMaxRhs) + 7) & ~7);
   a.stage_x = (xcs == 1 && xrs % 2 == 0 && b % 2 == 0 && ((uintptr_t)x & 15) == 0) ? 1 : 0;
   a.ncmax = adj ? (int)st.R : (int)st.C;  // gather list length per block (forward: in, adjoint: out)
-  if (ncta == 0) return;
+  if (ncta == 0) return true;
   switch (g_tc_mode * 2 + (adj ? 1 : 0)) {
-    case 2 * kTcTF32: launch_tc_dir<false, kTcTF32>(a, ncta, s); break;
-    case 2 * kTcTF32 + 1: launch_tc_dir<true, kTcTF32>(a, ncta, s); break;
-    case 2 * kTcBF16: launch_tc_dir<false, kTcBF16>(a, ncta, s); break;
-    case 2 * kTcBF16 + 1: launch_tc_dir<true, kTcBF16>(a, ncta, s); break;
-    case 2 * kTcX3: launch_tc_dir<false, kTcX3>(a, ncta, s); break;
-    default: launch_tc_dir<true, kTcX3>(a, ncta, s); break;
+    case 2 * kTcTF32: return launch_tc_var<false, kTcTF32>(a, ncta, s, var);
+    case 2 * kTcTF32 + 1: return launch_tc_var<true, kTcTF32>(a, ncta, s, var);
+    case 2 * kTcBF16: return launch_tc_var<false, kTcBF16>(a, ncta, s, var);
+    case 2 * kTcBF16 + 1: return launch_tc_var<true, kTcBF16>(a, ncta, s, var);
+    case 2 * kTcX3: return launch_tc_var<false, kTcX3>(a, ncta, s, var);
+    default: return launch_tc_var<true, kTcX3>(a, ncta, s, var);
   }
 }
 
@@ -615,7 +647,9 @@ void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long lon
                   long long yrs, long long ycs, int b, cudaStream_t s) {
   if (st.nblk == 0) return;
   if (use_tc<V>(st, b)) {
-    launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s);
+    const int tv = st.var[2 + g_tc_mode][adj ? 1 : 0][rhs_bucket(b)];
+    if (!launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s, tv))
+      launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s, 0);
     return;
   }
   const StageArgs<V> a = stage_args<V>(st, adj, x, xrs, xcs, y, yrs, ycs, b);
@@ -885,14 +919,15 @@ extern "C" int fio_apply_profiled(fio_op op, int which, const void* x, void* y, 
 // ---------------------------------------------------------------------------------------------
 namespace {
 
-// time one launch of variant `var` (best of 3 after one warm-up); < 0 when it does not apply
-template <typename V, bool ADJ>
-float time_variant(const StageArgs<V>& a, cudaStream_t s, int var, cudaEvent_t e0, cudaEvent_t e1) {
-  if (!launch_variant<V, ADJ>(a, s, var)) return -1.f;
+// time a launcher (best of 3 after one warm-up): the launcher returns false when its variant does
+// not apply (-1); -2 on a CUDA error
+template <typename F>
+float time_launch(F&& launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  if (!launch()) return -1.f;
   float best = -1.f;
   for (int rep = 0; rep < 3; ++rep) {
     cudaEventRecord(e0, s);
-    launch_variant<V, ADJ>(a, s, var);
+    launch();
     cudaEventRecord(e1, s);
     float ms = 0.f;
     if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -2.f;
@@ -900,6 +935,8 @@ float time_variant(const StageArgs<V>& a, cudaStream_t s, int var, cudaEvent_t e
   }
   return best;
 }
+
+constexpr int kTcCand[4] = {0, 10, 11, 12};
 
 // tune every stage launch of one vector type at b right-hand sides; choices[] gets the variant
 // per (stage, direction) in stage order, forward before adjoint
@@ -919,7 +956,7 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
     cudaEventDestroy(e0);
     return FIO_ECUDA;
   }
-  const int bucket = rhs_bucket(b), ti = type_index<V>();
+  const int bucket = rhs_bucket(b);
   int n = 0;
   rc = FIO_OK;
   for (int si = 0; si < (int)op->st.size() && rc == FIO_OK; ++si) {
@@ -927,13 +964,25 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
     const bool root = si >= op->n_bf + op->n_hif;
     for (int dir = 0; dir < (root ? 1 : 2) && rc == FIO_OK; ++dir) {
       const bool adj = dir == 1;
+      const bool tc = use_tc<V>(st, b);
+      const int ti = tc ? 2 + g_tc_mode : type_index<V>();
       int best = 0;
-      if (st.nblk > 0 && !use_tc<V>(st, b)) {
+      if (st.nblk > 0) {
         const StageArgs<V> a = stage_args<V>(st, adj, X, b, 1, Y, b, 1, b);
         float tbest = -1.f;
-        for (int k = 0; k < 5 && kCand[bucket][k] > 0; ++k) {
-          const int var = kCand[bucket][k];
-          const float t = adj ? time_variant<V, true>(a, s, var, e0, e1) : time_variant<V, false>(a, s, var, e0, e1);
+        const int ncand = tc ? 4 : 5;
+        for (int k = 0; k < ncand; ++k) {
+          const int var = tc ? kTcCand[k] : kCand[bucket][k];
+          if (var <= 0 && !tc) break;
+          float t;
+          if (tc) {
+            t = time_launch([&] { return launch_tc(st, adj, (const float2*)X, b, 1, (float2*)Y, b, 1, b, s, var); },
+                            s, e0, e1);
+          } else if (adj) {
+            t = time_launch([&] { return launch_variant<V, true>(a, s, var); }, s, e0, e1);
+          } else {
+            t = time_launch([&] { return launch_variant<V, false>(a, s, var); }, s, e0, e1);
+          }
           if (t == -2.f || cudaGetLastError() != cudaSuccess) {
             rc = FIO_ECUDA;
             break;
@@ -943,6 +992,7 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
             best = var;
           }
         }
+        if (rc == FIO_OK && tc && fio_tc_timeout_reset() != 0) rc = FIO_ETIMEOUT;
       }
       st.var[ti][dir][bucket] = (int8_t)best;
       if (choices && n < cap) choices[n] = best;
@@ -956,6 +1006,23 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
 }
 
 }  // namespace
+
+extern "C" int fio_set_variant(fio_op op, int b, int precision, int variant) {
+  if (!op || b <= 0 || precision < FIO_P64 || precision > FIO_PDF) return FIO_EINVAL;
+  const int bucket = rhs_bucket(b);
+  const int mode = tc_mode_of(precision);
+  const bool tc = mode != 0 && b >= 8;
+  int ti;
+  if (tc) {
+    if (variant != 0 && (variant < 10 || variant > 12)) return FIO_EINVAL;
+    ti = 2 + mode;
+  } else {
+    if (variant < 0 || variant > 8 || (variant == 8 && b > kVecMaxRhs)) return FIO_EINVAL;
+    ti = precision == FIO_P64 ? 0 : (precision == FIO_PDF ? 2 : 1);
+  }
+  for (auto& st : op->st) st.var[ti][0][bucket] = st.var[ti][1][bucket] = (int8_t)variant;
+  return FIO_OK;
+}
 
 extern "C" int fio_autotune(fio_op op, int b, int precision, void* stream, int* choices, int cap, int* nchoices) {
   if (!op || b < 0 || cap < 0 || (cap > 0 && !choices)) return FIO_EINVAL;

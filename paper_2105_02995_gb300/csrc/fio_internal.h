@@ -39,9 +39,10 @@ struct Stage {
   const int2* t128_fwd = nullptr;
   const int2* t128_adj = nullptr;
   int n128_fwd = 0, n128_adj = 0;
-  // kernel variant chosen by fio_autotune per [vector type: c128, c64, double-float][direction:
-  // forward, adjoint][right-hand-side bucket]; 0 = the built-in choice (see fio_capi.cu)
-  int8_t var[3][2][5] = {};
+  // kernel variant chosen by fio_autotune per [arithmetic: c128, c64, double-float, TF32, BF16,
+  // split TF32][direction: forward, adjoint][right-hand-side bucket]; 0 = the built-in choice
+  // (see fio_capi.cu)
+  int8_t var[6][2][5] = {};
 };
 
 }  // namespace fio

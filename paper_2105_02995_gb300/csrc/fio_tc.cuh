@@ -135,6 +135,13 @@ __device__ __forceinline__ void cp16(uint32_t dst, const void* src, int bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+// arrive on `bar` once every cp.async this thread issued so far has landed (counts as one arrival)
+__device__ __forceinline__ void cp_mbar_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(bar)) : "memory");
+}
 
 // byte offset of (row, 16-byte chunk) in a K-major 128-byte-swizzled tile
 __device__ __forceinline__ uint32_t swz(int row, int chunk) {
@@ -353,6 +360,229 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
       }
     }
   }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncol_tmem);
+}
+
+// ---- warp-specialised ring variant ----------------------------------------------------------
+// Same product and operand layout as k_stage_tc, with S chunk stages in shared memory and the
+// work split by role so that copies, B expansion and MMAs of different chunks overlap inside
+// one CTA (192 threads):
+//   warp 4      producer: 16-byte cp.async of chunk k's A tile and gathered x rows into stage
+//               k mod S, once the MMAs of chunk k - S have released it (mbarrier `empty`); the
+//               copies' completion arrives on `full` (cp.async.mbarrier.arrive.noinc);
+//   warps 0-3   expand the staged x rows into the B tile (split mode: also split the A tile),
+//               fence the writes to the async proxy and arrive on `bready`; after the last
+//               chunk they read the accumulator out of TMEM (lane quadrant = warp) and store;
+//   warp 5      lane 0 issues the chunk's MMAs when `bready` completes and commits them to
+//               `empty` (and, after the last chunk, to `done`).
+// Every wait is bounded (kWaitNs): a role that gives up stops, the others give up in turn, the
+// timeout is recorded, and the CTA still waits for its copies and MMAs before freeing TMEM.
+__host__ __device__ constexpr int tc_ring_stage_bytes(int mode, int N) {
+  return (((mode == kTcX3 ? 2 : 1) * (16384 + N * 128) + (mode == kTcBF16 ? 32 : 16) * (N / 2) * 8) + 1023) &
+         ~1023;
+}
+__host__ __device__ constexpr int tc_ring_smem_bytes(int mode, int N, int ncmax, int S) {
+  return S * tc_ring_stage_bytes(mode, N) + 1024 + ((ncmax + 3) & ~3) * 4;
+}
+
+template <bool ADJ, int MODE, int S>
+__global__ void __launch_bounds__(192) k_stage_tc_ring(TcArgs a) {
+  using namespace tc;
+  constexpr bool BF16 = MODE == kTcBF16;
+  constexpr bool X3 = MODE == kTcX3;
+  constexpr uint32_t TA = X3 ? 32768u : 16384u;
+  constexpr int ESZ = BF16 ? 4 : 8;  // bytes per complex entry of A
+  constexpr int KC = 128 / ESZ;      // complex columns per 128-byte chunk
+  constexpr int CPC = 16 / ESZ;      // complex entries per 16-byte copy
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_full[S];
+  __shared__ __align__(8) uint64_t s_bready[S];
+  __shared__ __align__(8) uint64_t s_empty[S];
+  __shared__ __align__(8) uint64_t s_done;
+  extern __shared__ __align__(16) uint8_t smem_dyn[];
+  const uint32_t base = (su32(smem_dyn) + 1023u) & ~1023u;
+  uint8_t* gbase = smem_dyn + (base - su32(smem_dyn));
+  const uint32_t TB = (uint32_t)a.nmax * 128;                  // one B tile (a multiple of 2048)
+  const uint32_t SB = (uint32_t)tc_ring_stage_bytes(MODE, a.nmax);
+  const uint32_t XOFF = TA + (X3 ? 2u : 1u) * TB;              // x staging inside a stage
+  int* sIdx = reinterpret_cast<int*>(gbase + S * SB);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int2 t = a.tiles[blockIdx.x];
+  const int blk = t.x, r0 = t.y * kTcRows;
+  const int2 d = a.dims[blk];
+  const int nrows = ADJ ? d.y : d.x, ncols = ADJ ? d.x : d.y;
+  const int j0 = blockIdx.y * kTcMaxRhs;
+  const int bcta = min(kTcMaxRhs, a.b - j0);
+  const int bp = (bcta + 7) & ~7;
+  const int N = 2 * bp;
+  const int sld = a.nmax / 2;
+  const uint32_t ncol_tmem = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+  const int* rowidx = a.rowidx + (size_t)blk * (ADJ ? a.ldc : a.ldr);
+  const int* colidx = a.colidx + (size_t)blk * (ADJ ? a.ldr : a.ldc);
+  const uint8_t* Ab = (const uint8_t*)a.A + (size_t)blk * a.bstride * ESZ;
+  const uint32_t id = idesc(BF16 ? 1u : 2u, kTcRows, N);
+  const int nchunks = (ncols + KC - 1) / KC;
+
+  if (warp == 0) tmem_alloc(&s_tmem, ncol_tmem);
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&s_full[q], 32);
+      mbar_init(&s_bready[q], 128);
+      mbar_init(&s_empty[q], 1);
+    }
+    mbar_init(&s_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int e = tid; e < ncols; e += 192) sIdx[e] = colidx[e];
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s_tmem;
+
+  bool ok = true;
+  if (warp == 4) {
+    // producer
+    for (int k = 0; k < nchunks && ok; ++k) {
+      const int st = k % S;
+      if (k >= S) ok = mbar_wait(&s_empty[st], (uint32_t)((k / S - 1) & 1));
+      if (!ok) break;
+      const uint32_t sA = base + st * SB, sX = sA + XOFF;
+      const int c0 = k * KC;
+      for (int e = lane; e < kTcRows * 8; e += 32) {
+        const int row = e >> 3, ch = e & 7;
+        const int gr = r0 + row, gc = c0 + ch * CPC;
+        const bool in = gr < nrows && gc < ncols;
+        const void* src = in ? (const void*)(Ab + ((size_t)gr * a.lda + gc) * ESZ) : a.A;
+        cp16(sA + swz(row, ch), src, in ? 16 : 0);
+      }
+      if (a.stage_x) {
+        const int cpr = bcta >> 1;
+        for (int e = lane; e < KC * cpr; e += 32) {
+          const int c = e / cpr, q = e - c * cpr;
+          const int idx = (c0 + c < ncols) ? sIdx[c0 + c] : -1;
+          const void* src = idx >= 0 ? (const void*)(a.x + (long long)idx * a.xrs + j0 + 2 * q) : (const void*)a.x;
+          cp16(sX + (uint32_t)((c * sld + 2 * q) * 8), src, idx >= 0 ? 16 : 0);
+        }
+      }
+      cp_mbar_arrive(&s_full[st]);
+    }
+    cp_wait_all();
+  } else if (warp == 5) {
+    // MMA issuer
+    if (lane == 0) {
+      for (int k = 0; k < nchunks && ok; ++k) {
+        const int st = k % S;
+        ok = mbar_wait(&s_bready[st], (uint32_t)((k / S) & 1));
+        if (!ok) break;
+        fence_after();
+        const uint32_t sA = base + st * SB, sB = sA + TA;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (X3) {
+            mma<false>(tmem, sdesc(sA + 16384 + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
+            mma<false>(tmem, sdesc(sA + 32 * q), sdesc(sB + TB + 32 * q), id, 1u);
+            mma<false>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, 1u);
+          } else {
+            mma<BF16>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit(&s_empty[st]);
+      }
+      if (nchunks > 0) {
+        // every MMA issued so far is finished before `done` completes (also after a timeout)
+        mma_commit(&s_done);
+        ok = mbar_wait(&s_done, 0) && ok;
+      }
+    }
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  } else {
+    // warps 0-3: B expansion (and the A split), then the epilogue
+    for (int k = 0; k < nchunks && ok; ++k) {
+      const int st = k % S;
+      ok = mbar_wait(&s_full[st], (uint32_t)((k / S) & 1));
+      if (!ok) break;
+      uint8_t* pA = gbase + st * SB;
+      uint8_t* pB = pA + TA;
+      const float2* pX = reinterpret_cast<const float2*>(pA + XOFF);
+      const int c0 = k * KC;
+      for (int e = tid; e < KC * bp; e += 128) {
+        const int c = e / bp, j = e - c * bp;
+        float2 v = make_float2(0.f, 0.f);
+        if (j < bcta) {
+          if (a.stage_x) {
+            v = pX[c * sld + j];
+          } else if (c0 + c < ncols) {
+            const int idx = sIdx[c0 + c];
+            if (idx >= 0) v = a.x[(long long)idx * a.xrs + (long long)(j0 + j) * a.xcs];
+          }
+        }
+        float p0, p1, q0, q1;
+        if (!ADJ) {
+          p0 = v.x; p1 = -v.y; q0 = v.y; q1 = v.x;
+        } else {
+          p0 = v.x; p1 = v.y; q0 = v.y; q1 = -v.x;
+        }
+        const int n0 = 2 * j, n1 = 2 * j + 1;
+        if (BF16) {
+          const int ch = c >> 2, off = (c & 3) << 2;
+          *reinterpret_cast<__nv_bfloat162*>(pB + swz(n0, ch) + off) = __floats2bfloat162_rn(p0, p1);
+          *reinterpret_cast<__nv_bfloat162*>(pB + swz(n1, ch) + off) = __floats2bfloat162_rn(q0, q1);
+        } else if (X3) {
+          const int ch = c >> 1, off = (c & 1) << 3;
+          const float hp0 = tf32_rna(p0), hp1 = tf32_rna(p1), hq0 = tf32_rna(q0), hq1 = tf32_rna(q1);
+          *reinterpret_cast<float2*>(pB + swz(n0, ch) + off) = make_float2(hp0, hp1);
+          *reinterpret_cast<float2*>(pB + swz(n1, ch) + off) = make_float2(hq0, hq1);
+          *reinterpret_cast<float2*>(pB + TB + swz(n0, ch) + off) =
+              make_float2(tf32_rna(p0 - hp0), tf32_rna(p1 - hp1));
+          *reinterpret_cast<float2*>(pB + TB + swz(n1, ch) + off) =
+              make_float2(tf32_rna(q0 - hq0), tf32_rna(q1 - hq1));
+        } else {
+          const int ch = c >> 1, off = (c & 1) << 3;
+          *reinterpret_cast<float2*>(pB + swz(n0, ch) + off) = make_float2(p0, p1);
+          *reinterpret_cast<float2*>(pB + swz(n1, ch) + off) = make_float2(q0, q1);
+        }
+      }
+      if (X3) {
+        for (int e = tid; e < kTcRows * 8; e += 128) {
+          float4* h = reinterpret_cast<float4*>(pA + 16 * e);
+          const float4 v = *h;
+          const float4 hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+          *h = hi;
+          *reinterpret_cast<float4*>(pA + 16384 + 16 * e) =
+              make_float4(tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z), tf32_rna(v.w - hi.w));
+        }
+      }
+      fence_async_smem();
+      mbar_arrive(&s_bready[st]);
+    }
+    if (nchunks > 0 && ok) ok = mbar_wait(&s_done, 0);
+    fence_after();
+    // epilogue: warp w holds accumulator rows 32w .. 32w+31 (TMEM lanes)
+    const int row = r0 + warp * 32 + lane;
+    const int oidx = (row < nrows) ? rowidx[row] : -1;
+    for (int cb = 0; cb < N; cb += 16) {
+      uint32_t r[16];
+      if (nchunks > 0 && ok) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, r);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) r[q] = 0u;
+      }
+      if (oidx >= 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = cb / 2 + q;
+          if (j < bcta)
+            a.y[(long long)oidx * a.yrs + (long long)(j0 + j) * a.ycs] =
+                make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+        }
+      }
+    }
+  }
+  if (!ok) atomicExch(&g_tc_timeout, 1);
   fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, ncol_tmem);

@@ -1,4 +1,4 @@
-"""Serving loop for inverse applies of several resident operators, with continuous batching.
+"""Serving loop for inverse applies or solves of several resident operators, with continuous batching.
 
 Requests (operator name, b complex64 right-hand sides, arrival time) arrive over time.  The loop:
   * admits a request when the device memory its batch needs fits the HBM budget (the factors of
@@ -9,6 +9,12 @@ Requests (operator name, b complex64 right-hand sides, arrival time) arrive over
   * batches of different operators run concurrently on their streams;
   * polls completion events without blocking; results go back to their requests, and the latency
     of a request is completion time minus arrival time.
+mode="apply": a request is the direct solve f = G-dot K-dot* u (complex64, one fio_apply_inv per
+batch).  mode="solve": a request is solved to a relative residual (fio_solve, iterative
+refinement by default: FP64 solution, double-float residuals, corrections in the serving
+precision); fio_solve synchronises its stream, so each operator gets one worker thread that runs
+its batches (ctypes releases the interpreter lock during the call) and batches of different
+operators still overlap on the device.
 Every step runs in libfio's kernels through the C ABI; this module only schedules.
 """
 
@@ -28,7 +34,8 @@ class Request:
     u: np.ndarray          # (N, b) complex64, host
     t_arrival: float       # seconds after the start of the run
     t_done: float = -1.0
-    f: np.ndarray = None   # (N, b) complex64, host, filled on completion
+    f: np.ndarray = None   # (N, b) host result (complex64 applies, complex128 solves)
+    info: list = None      # solve mode: (iterations, relative residual, status) per column
 
 
 @dataclass
@@ -62,14 +69,24 @@ class ServeStats:
 
 class Server:
     def __init__(self, ops: dict, max_batch: int = 64, hbm_budget: int | None = None,
-                 precision: int | None = None):
+                 precision: int | None = None, mode: str = "apply", solve_kw: dict | None = None):
         import torch
         from . import binding
+        if mode not in ("apply", "solve"):
+            raise ValueError("mode is 'apply' or 'solve'")
         self.torch = torch
         self.binding = binding
         self.ops = ops
         self.max_batch = max_batch
         self.precision = precision
+        self.mode = mode
+        self.solve_kw = dict(method=binding.FIO_IR, tol=1e-10, maxit=60, outer=binding.FIO_PDF,
+                             inner=binding.FIO_P32 if precision is None else precision)
+        self.solve_kw.update(solve_kw or {})
+        self.workers = {}
+        if mode == "solve":
+            from concurrent.futures import ThreadPoolExecutor
+            self.workers = {name: ThreadPoolExecutor(max_workers=1) for name in ops}
         self.streams = {name: torch.cuda.Stream() for name in ops}
         resident = sum(op.device_bytes() for op in ops.values())
         free, total = torch.cuda.mem_get_info()
@@ -78,7 +95,18 @@ class Server:
 
     def _batch_bytes(self, name, b):
         N = self.ops[name].N
+        if self.mode == "solve":  # u, f in complex128 and the solver's work vectors
+            return (8 + self.solve_kw.get("restart", 20)) * N * b * 16
         return 2 * N * b * 8  # device u and f of the batch (complex64)
+
+    def _solve_batch(self, name, uh):
+        """Runs in the operator's worker thread: one fio_solve of the batch on its stream."""
+        torch = self.torch
+        op = self.ops[name]
+        with torch.cuda.stream(self.streams[name]):
+            u = self.binding.colmajor(torch.from_numpy(uh.T.copy()).to("cuda", torch.complex128).t())
+            f, infos = op.solve(u, **self.solve_kw)
+            return f.t().contiguous().cpu().numpy().T, infos
 
     def warmup(self):
         """One launch per operator and batch width class, so scratch pools are sized up front."""
@@ -88,6 +116,9 @@ class Server:
                 for b in sorted({1, 2, 4, 8, 16, 32, self.max_batch}):
                     u = self.binding.colmajor(torch.zeros((op.N, b), dtype=torch.complex64, device="cuda"))
                     op.apply_inv(u, precision=self.precision)
+                    if self.mode == "solve":
+                        u1 = self.binding.colmajor(torch.ones((op.N, b), dtype=torch.complex128, device="cuda"))
+                        op.solve(u1, **self.solve_kw)
         torch.cuda.synchronize()
 
     def run(self, requests: list, poll_sleep: float = 0.0) -> ServeStats:
@@ -120,11 +151,16 @@ class Server:
                 st.max_inflight_bytes = max(st.max_inflight_bytes, inflight_bytes)
             for name, op in self.ops.items():
                 bt = inflight[name]
-                if bt is not None and bt.event.query():
+                if bt is not None and (bt.event.done() if self.mode == "solve" else bt.event.query()):
                     tnow = time.perf_counter() - t0
-                    fh = bt.f_host.numpy()
+                    if self.mode == "solve":
+                        fh, infos = bt.event.result()
+                    else:
+                        fh, infos = bt.f_host.numpy(), None
                     for r, (c0, c1) in zip(bt.reqs, bt.cols):
                         r.f = fh[:, c0:c1].copy()
+                        if infos is not None:
+                            r.info = infos[c0:c1]
                         r.t_done = tnow
                         st.latencies_ms.append(1000 * (tnow - r.t_arrival))
                         inflight_bytes -= reserved.pop(r.rid)
@@ -143,6 +179,13 @@ class Server:
                     uh = np.empty((op.N, bsum), dtype=np.complex64, order="F")
                     for r, (c0, c1) in zip(batch, cols):
                         uh[:, c0:c1] = r.u
+                    st.launches += 1
+                    st.rhs += bsum
+                    st.rhs_N += bsum * op.N
+                    if self.mode == "solve":
+                        fut = self.workers[name].submit(self._solve_batch, name, uh)
+                        inflight[name] = _Batch(batch, fut, None, cols, 0)
+                        continue
                     s = self.streams[name]
                     with torch.cuda.stream(s):
                         ut = torch.from_numpy(uh.T.copy()).pin_memory().to("cuda", non_blocking=True).t()
@@ -151,9 +194,6 @@ class Server:
                         fh.copy_(fd.t(), non_blocking=True)
                         ev = torch.cuda.Event()
                         ev.record(s)
-                    st.launches += 1
-                    st.rhs += bsum
-                    st.rhs_N += bsum * op.N
                     inflight[name] = _Batch(batch, ev, _T(fh), cols, 0)
             if poll_sleep:
                 time.sleep(poll_sleep)
@@ -201,6 +241,7 @@ def main(argv=None):
     ap.add_argument("--load", type=float, default=0.7, help="offered load as a fraction of capacity")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "tf32x3"])
     ap.add_argument("--seed", type=int, default=2105_02995 + 4000)
+    ap.add_argument("--mode", default="apply", choices=["apply", "solve"])
     a = ap.parse_args(argv)
     fbuild.build()
     prec = {"fp32": binding.FIO_P32, "tf32": binding.FIO_PTF32, "bf16": binding.FIO_PBF16,
@@ -210,7 +251,7 @@ def main(argv=None):
         kind, n, eb, eh = spec.split(":")
         buf, _ = build_cached(kind, int(n), float(eb), float(eh), gpu=True, verbose=False)
         ops[f"{kind}_{n}"] = binding.Operator(buf)
-    srv = Server(ops, precision=prec)
+    srv = Server(ops, precision=prec, mode=a.mode)
     srv.warmup()
     # capacity probe: back-to-back batches of 32 on every operator
     probe = poisson_requests(ops, 4 * len(ops), 1e9, a.seed, b_range=(32, 32))
@@ -218,7 +259,7 @@ def main(argv=None):
     rate = a.load * cap / 32.5  # requests per second (mean 32.5 right-hand sides each)
     reqs = poisson_requests(ops, a.requests, rate, a.seed)
     stats = srv.run(reqs)
-    out = {"mix": sorted(ops), "precision": a.precision, "capacity_rhs_per_s": cap,
+    out = {"mix": sorted(ops), "mode": a.mode, "precision": a.precision, "capacity_rhs_per_s": cap,
            "offered_requests_per_s": rate, **stats.summary()}
     print(json.dumps(out))
 

@@ -1,12 +1,12 @@
 """Synthetic one-stage benchmark of the stage kernels (for tuning and profiling them).
 
     python -m paper_2105_02995_gb300.stagebench [--nblk 1024] [--rows 512] [--cols 512]
-        [--b 8,32,64] [--prec fp32,tf32,bf16] [--reps 5]
+        [--b 8,32,64] [--prec fp32,tf32,bf16] [--variants 0] [--reps 5]
 
 Builds a packed operator whose first butterfly-type stage holds nblk random dense complex blocks
 of rows x cols with random gather and scatter permutations (a second stage of 16 x 16 identity
 blocks closes the chain), uploads it through the C ABI and times that first stage of apply_K
-with fio_apply_profiled (CUDA events around the launch), for each precision and batch width.
+with fio_apply_profiled (CUDA events around the launch), for each precision, batch width and kernel variant (fio_set_variant; 0 = the built-in choice).
 Prints one JSON object: per configuration the median time, the stage's complex flops rate
 (8 b entries / t) and the rate at which its factor entries are streamed (entry bytes / t).
 No method arithmetic is involved: the blocks are random.
@@ -27,6 +27,7 @@ def main(argv=None):
     ap.add_argument("--cols", type=int, default=512)
     ap.add_argument("--b", default="8,32,64")
     ap.add_argument("--prec", default="fp32,tf32,bf16")
+    ap.add_argument("--variants", default="0", help="kernel variants to pin (fio_set_variant)")
     ap.add_argument("--reps", type=int, default=5)
     a = ap.parse_args(argv)
     import torch
@@ -59,14 +60,21 @@ def main(argv=None):
         y = binding.colmajor(torch.empty_like(x))
         for name in a.prec.split(","):
             p = precs[name]
-            for _ in range(2):
-                op.apply_profiled("K", x, y, precision=p)
-            # launch groups of apply_K with b >= 5: [layout change, stage 1, stage 2]
-            ts = [op.apply_profiled("K", x, y, precision=p)[1] for _ in range(a.reps)]
-            ms = float(np.median(ts))
-            ent = nblk * R * C
-            out[f"{name}_b{b}"] = {"ms": round(ms, 4), "tflops": round(8 * ent * b / ms / 1e9, 1),
-                                   "factor_gbs": round(ent * (4 if name == "bf16" else 8) / ms / 1e6, 1)}
+            for var in [int(v) for v in a.variants.split(",")]:
+                try:
+                    op.set_variant(b, p, var)
+                except binding.FioError:
+                    continue  # no such variant for this precision and batch
+                for _ in range(2):
+                    op.apply_profiled("K", x, y, precision=p)
+                # launch groups of apply_K with b >= 5: [layout change, stage 1, stage 2]
+                ts = [op.apply_profiled("K", x, y, precision=p)[1] for _ in range(a.reps)]
+                ms = float(np.median(ts))
+                ent = nblk * R * C
+                tag = f"{name}_b{b}" + (f"_v{var}" if var else "")
+                out[tag] = {"ms": round(ms, 4), "tflops": round(8 * ent * b / ms / 1e9, 1),
+                            "factor_gbs": round(ent * (4 if name == "bf16" else 8) / ms / 1e6, 1)}
+            op.set_variant(b, p, 0)
     print(json.dumps(out))
     op.release()
 

@@ -331,3 +331,64 @@ def test_autotune_rejects_bad_arguments():
     assert lib.fio_autotune(op.h, 4, 9, None, None, 0, ctypes.byref(n)) == -1
     assert lib.fio_autotune(op.h, 4, binding.FIO_P64, None, None, 5, ctypes.byref(n)) == -1  # cap > 0, no array
     assert lib.fio_autotune(op.h, 0, binding.FIO_P64, None, None, 0, ctypes.byref(n)) == 0 and n.value == 0
+
+
+@pytest.mark.parametrize("name", ["ex1_1024", "ex3_32"])
+@pytest.mark.parametrize("prec,dt", [(binding.FIO_P64, torch.complex128), (binding.FIO_P32, torch.complex64),
+                                     (binding.FIO_PDF, torch.complex128)])
+def test_every_tile_shape_is_bit_identical(name, prec, dt):
+    """Each tile shape <TX,TB,TR> of the stage kernel sums every output's terms in the same
+    order, so pinning any of them reproduces the built-in choice bit for bit (b = 40: ragged RHS
+    tiles for every shape)."""
+    buf, info, P, op, ofo = get(name)
+    b = 40
+    xd = dev(complex_gaussian(ofo.N, b, rhs_seed(0, 700)), dt)
+    op.set_variant(b, prec, 0)
+    ref = {w: getattr(op, "apply_" + w)(xd, precision=prec).clone() for w in ("K", "Kadj", "inv")}
+    for var in range(1, 8):
+        op.set_variant(b, prec, var)
+        for w in ("K", "Kadj", "inv"):
+            y = getattr(op, "apply_" + w)(xd, precision=prec)
+            torch.cuda.synchronize()
+            assert torch.equal(y, ref[w]), (var, w)
+    op.set_variant(b, prec, 0)
+
+
+@pytest.mark.parametrize("name", ["ex1_256", "ex3_32"])
+@pytest.mark.parametrize("prec", TC_PRECS)
+@pytest.mark.parametrize("b", [8, 40, 72])
+def test_tensor_core_ring_matches_single_buffer(name, prec, b):
+    """The warp-specialised ring kernel (2, 3, 4 chunk stages) issues the same MMAs in the same
+    order as the single-buffer kernel: bit-identical results, and within the precision's bound
+    of the oracle."""
+    buf, info, P, op, ofo = get(name)
+    lib = binding.load()
+    x = complex_gaussian(ofo.N, b, rhs_seed(0, 800 + b))
+    xd = dev(x, torch.complex64)
+    x64 = x.astype(np.complex64).astype(np.complex128)
+    op.set_variant(b, prec, 0)
+    ref = {}
+    for w, fn in (("K", lib.fio_apply_K), ("Kadj", lib.fio_apply_Kadj), ("inv", lib.fio_apply_inv)):
+        rc, y = _tc_apply(op, fn, xd, b, prec)
+        assert rc == 0
+        ref[w] = y.clone()
+    for var in (10, 11, 12):
+        op.set_variant(b, prec, var)
+        for w, fn, oref in (("K", lib.fio_apply_K, fa.apply_Kdot), ("Kadj", lib.fio_apply_Kadj, fa.apply_Kdot_adj),
+                            ("inv", lib.fio_apply_inv, fa.apply_inv)):
+            rc, y = _tc_apply(op, fn, xd, b, prec)
+            assert rc == 0, (var, w, rc)
+            assert torch.equal(y, ref[w]), (var, w)
+            assert rel(host(y), oref(P, x64)) < TOL_TC[prec], (var, w)
+    op.set_variant(b, prec, 0)
+
+
+def test_set_variant_rejects_unknown_variants():
+    buf, info, P, op, ofo = get("ex3_32")
+    lib = binding.load()
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 9) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 8) == -1    # few-RHS kernel needs b <= 4
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_PTF32, 3) == -1  # tensor-core launch: 0, 10-12
+    assert lib.fio_set_variant(op.h, 0, binding.FIO_P32, 1) == -1
+    assert lib.fio_set_variant(op.h, 4, binding.FIO_P32, 8) == 0
+    assert lib.fio_set_variant(op.h, 4, binding.FIO_P32, 0) == 0

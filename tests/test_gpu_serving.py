@@ -77,3 +77,26 @@ def test_serving_admission_respects_budget():
     st = srv.run(reqs)
     assert st.max_inflight_bytes <= 2 * one
     assert len(st.latencies_ms) == len(reqs)
+
+
+def test_serving_solve_mode_results_equal_alone():
+    """Solve requests (iterative refinement to 1e-10: double-float residuals, FP32 corrections),
+    batched per operator and run by one worker thread per operator: every request converges, and
+    its solution equals the same request solved alone to within what two solutions with relative
+    residual <= 1e-10 can differ by on these well-conditioned operators (1e-8)."""
+    o = ops()
+    reqs = poisson_requests(o, 24, rate_per_s=5000.0, seed=777, b_range=(1, 12))
+    srv = Server(o, max_batch=64, mode="solve")
+    srv.warmup()
+    st = srv.run(reqs)
+    assert st.summary()["requests"] == len(reqs)
+    assert st.launches < len(reqs)
+    for r in reqs:
+        assert r.f.dtype == np.complex128 and r.f.shape == r.u.shape
+        assert all(s == 0 and rr <= 1e-10 for _, rr, s in r.info), r.info
+        op = o[r.op]
+        ud = binding.colmajor(torch.from_numpy(r.u.astype(np.complex128)).cuda())
+        alone, infos = op.solve(ud, **srv.solve_kw)
+        alone = alone.cpu().numpy()
+        err = np.linalg.norm(r.f - alone) / np.linalg.norm(alone)
+        assert err < 1e-8, (r.rid, r.op, r.u.shape, err)
