@@ -169,9 +169,10 @@ int fio_solve(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
  * and bucket use the choice; untuned ones keep the built-in choice by b.  Variants: 1..7 tile
  * shapes <TX,TB,TR> of the tiled stage kernel (1 <8,1,2>, 2 <16,1,4>, 3 <16,2,4>, 4 <8,2,2>,
  * 5 <8,4,2>, 6 <32,1,8>, 7 <16,4,4>: TX x TB right-hand sides and 64 rows per 256-thread CTA),
- * 8 the few-right-hand-side kernel (b <= 4); with a tensor-core precision and b >= 8: 0 the
- * single-buffer tcgen05 kernel, 10 / 11 / 12 its warp-specialised ring variant with 2 / 3 / 4
- * chunk stages; 0 also for empty stages.
+ * 8 the few-right-hand-side kernel (b <= 4), 9 / 10 complex64 tiles with contiguous per-thread
+ * rows and right-hand sides (<16,2,8> on 128 threads, <16,2,4> on 256); with a tensor-core
+ * precision and b >= 8: 0 the single-buffer tcgen05 kernel, 20 / 21 / 22 its warp-specialised
+ * ring variant with 2 / 3 / 4 chunk stages; 0 also for empty stages.
  * Every variant sums each output's terms in the same order, except 8 (tree reductions), so
  * results for b >= 5 do not depend on the choice.  choices (may be NULL when cap == 0) receives
  * the variant per stage launch in stage order, forward before adjoint (the root: forward
@@ -180,8 +181,9 @@ int fio_solve(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
 int fio_autotune(fio_op op, int b, int precision, void* stream, int* choices, int cap, int* nchoices);
 
 /* Pin the kernel variant of every stage launch of (precision, the bucket of b) to `variant`
- * (0 = the built-in choice): 1..8 as for fio_autotune on the CUDA cores (8 only for b <= 4);
- * with a tensor-core precision and b >= 8, 0 (single-buffer kernel) or 10, 11, 12 (the
+ * (0 = the built-in choice): 1..10 as for fio_autotune on the CUDA cores (8 only for b <= 4, 9
+ * and 10 only for FIO_P32); with a tensor-core precision and b >= 8, 0 (single-buffer kernel)
+ * or 20, 21, 22 (the
  * warp-specialised ring kernel with 2, 3, 4 chunk stages; variants whose shared memory does not
  * fit fall back to 0).  Host-only; FIO_EINVAL for a variant that does not exist for the pair. */
 int fio_set_variant(fio_op op, int b, int precision, int variant);

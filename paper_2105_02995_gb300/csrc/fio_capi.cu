@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <new>
 #include <vector>
 
@@ -414,6 +415,33 @@ void launch_pipe(StageArgs<V> a, cudaStream_t s) {
   k_stage_mm_pipe<V, ADJ, TX, TB, TR, CK><<<grid, 256, S::SMEM, s>>>(a);
 }
 
+// complex64 tiles with contiguous per-thread rows and right-hand sides (k_stage_mm_vt)
+template <bool ADJ, int TX, int TB, int TR, int NT>
+void launch_vt(StageArgs<float2> a, cudaStream_t s) {
+  using S = VtShape<ADJ, TX, TB, TR, NT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_stage_mm_vt<ADJ, TX, TB, TR, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    attr = true;
+  }
+  static_assert(S::RT == kTileRows, "tile lists are built for 64-row tiles");
+  const int nrows = ADJ ? a.C : a.R;
+  a.ntiles = (nrows + S::RT - 1) / S::RT;
+  const long long ncta = a.tiles ? a.ntiles_list : (long long)a.nblk * a.ntiles;
+  if (ncta == 0) return;
+  dim3 grid((unsigned)ncta, (unsigned)((a.b + S::BT - 1) / S::BT));
+  k_stage_mm_vt<ADJ, TX, TB, TR, NT><<<grid, NT, S::SMEM, s>>>(a);
+}
+template <typename V, bool ADJ, int TX, int TB, int TR, int NT>
+bool launch_vt_if(const StageArgs<V>& a, cudaStream_t s) {
+  if constexpr (std::is_same<V, float2>::value) {
+    launch_vt<ADJ, TX, TB, TR, NT>(a, s);
+    return true;
+  } else {
+    return false;
+  }
+}
+
 // the pipelined kernel needs row-major x with 16-byte aligned rows of M and of x
 template <typename V>
 bool pipe_ok(const StageArgs<V>& a) {
@@ -459,11 +487,15 @@ bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
 // ---- kernel variants (the autotuner's candidates) -----------------------------------------
 // 1..7: tile shapes <TX, TB, TR> of the tiled kernel (256 threads, 64-row tiles, TX x TB
 // right-hand sides per CTA): 1 <8,1,2>, 2 <16,1,4>, 3 <16,2,4>, 4 <8,2,2>, 5 <8,4,2>,
-// 6 <32,1,8>, 7 <16,4,4>; 8: k_stage_vec (b <= 4).  Shapes 2..7 need the pipelined kernel's
-// layout (row-major, 16-byte aligned rows); shape 1 falls back to the plain tiled kernel.
+// 6 <32,1,8>, 7 <16,4,4>; 8: k_stage_vec (b <= 4); complex64 only, contiguous per-thread tiles
+// (k_stage_mm_vt): 9 <16,2,8> with 128 threads, 10 <16,2,4> with 256 threads.  Shapes 2..7, 9, 10
+// need the pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the
+// plain tiled kernel.
 inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : (b <= 32 ? 3 : 4))); }
 // candidates per bucket, the built-in choice first
-constexpr int kCand[5][5] = {{8, 1, 0, 0, 0}, {1, 2, 0, 0, 0}, {2, 4, 3, 0, 0}, {3, 5, 6, 0, 0}, {3, 5, 6, 7, 0}};
+constexpr int kNCand = 6;
+constexpr int kCand[5][kNCand] = {{8, 1, 0, 0, 0, 0}, {1, 2, 0, 0, 0, 0}, {2, 4, 3, 0, 0, 0},
+                                  {3, 5, 6, 9, 10, 0}, {3, 5, 6, 7, 9, 10}};
 
 // launch with variant `var`; false when it does not apply to this launch
 template <typename V, bool ADJ>
@@ -481,6 +513,8 @@ bool launch_variant(const StageArgs<V>& a, cudaStream_t s, int var) {
     case 6: if (!pipe) return false; launch_pipe<V, ADJ, 32, 1, 8>(a, s); return true;
     case 7: if (!pipe) return false; launch_pipe<V, ADJ, 16, 4, 4>(a, s); return true;
     case 8: return a.b <= kVecMaxRhs && launch_vec<V, ADJ>(a, s);
+    case 9: return pipe && launch_vt_if<V, ADJ, 16, 2, 8, 128>(a, s);
+    case 10: return pipe && launch_vt_if<V, ADJ, 16, 2, 4, 256>(a, s);
     default: return false;
   }
 }
@@ -550,14 +584,14 @@ bool launch_tc_ring(const TcArgs& a, int ncta, cudaStream_t s) {
   return true;
 }
 
-// tensor-core variants: 0 the single-buffer kernel, 10 + (S - 2) the ring kernel with S stages
+// tensor-core variants: 0 the single-buffer kernel, 20 + (S - 2) the ring kernel with S stages
 template <bool ADJ, int MODE>
 bool launch_tc_var(const TcArgs& a, int ncta, cudaStream_t s, int var) {
   switch (var) {
     case 0: launch_tc_dir<ADJ, MODE>(a, ncta, s); return true;
-    case 10: return launch_tc_ring<ADJ, MODE, 2>(a, ncta, s);
-    case 11: return launch_tc_ring<ADJ, MODE, 3>(a, ncta, s);
-    case 12: return launch_tc_ring<ADJ, MODE, 4>(a, ncta, s);
+    case 20: return launch_tc_ring<ADJ, MODE, 2>(a, ncta, s);
+    case 21: return launch_tc_ring<ADJ, MODE, 3>(a, ncta, s);
+    case 22: return launch_tc_ring<ADJ, MODE, 4>(a, ncta, s);
     default: return false;
   }
 }
@@ -936,7 +970,7 @@ float time_launch(F&& launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   return best;
 }
 
-constexpr int kTcCand[4] = {0, 10, 11, 12};
+constexpr int kTcCand[4] = {0, 20, 21, 22};
 
 // tune every stage launch of one vector type at b right-hand sides; choices[] gets the variant
 // per (stage, direction) in stage order, forward before adjoint
@@ -970,7 +1004,7 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
       if (st.nblk > 0) {
         const StageArgs<V> a = stage_args<V>(st, adj, X, b, 1, Y, b, 1, b);
         float tbest = -1.f;
-        const int ncand = tc ? 4 : 5;
+        const int ncand = tc ? 4 : kNCand;
         for (int k = 0; k < ncand; ++k) {
           const int var = tc ? kTcCand[k] : kCand[bucket][k];
           if (var <= 0 && !tc) break;
@@ -1014,11 +1048,12 @@ extern "C" int fio_set_variant(fio_op op, int b, int precision, int variant) {
   const bool tc = mode != 0 && b >= 8;
   int ti;
   if (tc) {
-    if (variant != 0 && (variant < 10 || variant > 12)) return FIO_EINVAL;
+    if (variant != 0 && (variant < 20 || variant > 22)) return FIO_EINVAL;
     ti = 2 + mode;
   } else {
-    if (variant < 0 || variant > 8 || (variant == 8 && b > kVecMaxRhs)) return FIO_EINVAL;
     ti = precision == FIO_P64 ? 0 : (precision == FIO_PDF ? 2 : 1);
+    if (variant < 0 || variant > 10 || (variant == 8 && b > kVecMaxRhs) || (variant >= 9 && ti != 1))
+      return FIO_EINVAL;
   }
   for (auto& st : op->st) st.var[ti][0][bucket] = st.var[ti][1][bucket] = (int8_t)variant;
   return FIO_OK;

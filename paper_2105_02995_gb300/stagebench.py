@@ -28,6 +28,7 @@ def main(argv=None):
     ap.add_argument("--b", default="8,32,64")
     ap.add_argument("--prec", default="fp32,tf32,bf16")
     ap.add_argument("--variants", default="0", help="kernel variants to pin (fio_set_variant)")
+    ap.add_argument("--dirs", default="fwd", help="fwd (the stage in apply_K) and/or adj (in apply_Kadj)")
     ap.add_argument("--reps", type=int, default=5)
     a = ap.parse_args(argv)
     import torch
@@ -65,15 +66,18 @@ def main(argv=None):
                     op.set_variant(b, p, var)
                 except binding.FioError:
                     continue  # no such variant for this precision and batch
-                for _ in range(2):
-                    op.apply_profiled("K", x, y, precision=p)
-                # launch groups of apply_K with b >= 5: [layout change, stage 1, stage 2]
-                ts = [op.apply_profiled("K", x, y, precision=p)[1] for _ in range(a.reps)]
-                ms = float(np.median(ts))
-                ent = nblk * R * C
-                tag = f"{name}_b{b}" + (f"_v{var}" if var else "")
-                out[tag] = {"ms": round(ms, 4), "tflops": round(8 * ent * b / ms / 1e9, 1),
-                            "factor_gbs": round(ent * (4 if name == "bf16" else 8) / ms / 1e6, 1)}
+                for d in a.dirs.split(","):
+                    # launch groups with b >= 5: apply_K [layout, stage 1, stage 2],
+                    # apply_Kadj [layout, stage 2 adjoint, stage 1 adjoint]
+                    which, grp = ("K", 1) if d == "fwd" else ("Kadj", 2)
+                    for _ in range(2):
+                        op.apply_profiled(which, x, y, precision=p)
+                    ts = [op.apply_profiled(which, x, y, precision=p)[grp] for _ in range(a.reps)]
+                    ms = float(np.median(ts))
+                    ent = nblk * R * C
+                    tag = f"{name}_b{b}" + (f"_v{var}" if var else "") + ("" if d == "fwd" else "_adj")
+                    out[tag] = {"ms": round(ms, 4), "tflops": round(8 * ent * b / ms / 1e9, 1),
+                                "factor_gbs": round(ent * (4 if name == "bf16" else 8) / ms / 1e6, 1)}
             op.set_variant(b, p, 0)
     print(json.dumps(out))
     op.release()

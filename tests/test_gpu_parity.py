@@ -292,7 +292,7 @@ def test_exact_initial_guess_needs_no_iteration(method):
 # Autotuner: every tile-shape variant sums each output's terms in the same order, so for b >= 5
 # the tuned applies must reproduce the built-in ones bit for bit; for b <= 4 the few-RHS kernel
 # (tree reductions) may be chosen, within the parity tolerances above.
-ALLOWED = {0: {0, 8, 1}, 1: {0, 1, 2}, 2: {0, 2, 3, 4}, 3: {0, 3, 5, 6}, 4: {0, 3, 5, 6, 7}}
+ALLOWED = {0: {0, 8, 1}, 1: {0, 1, 2}, 2: {0, 2, 3, 4}, 3: {0, 3, 5, 6, 9, 10}, 4: {0, 3, 5, 6, 7, 9, 10}}
 
 
 def _bucket(b):
@@ -345,7 +345,7 @@ def test_every_tile_shape_is_bit_identical(name, prec, dt):
     xd = dev(complex_gaussian(ofo.N, b, rhs_seed(0, 700)), dt)
     op.set_variant(b, prec, 0)
     ref = {w: getattr(op, "apply_" + w)(xd, precision=prec).clone() for w in ("K", "Kadj", "inv")}
-    for var in range(1, 8):
+    for var in list(range(1, 8)) + ([9, 10] if prec == binding.FIO_P32 else []):
         op.set_variant(b, prec, var)
         for w in ("K", "Kadj", "inv"):
             y = getattr(op, "apply_" + w)(xd, precision=prec)
@@ -358,7 +358,7 @@ def test_every_tile_shape_is_bit_identical(name, prec, dt):
 @pytest.mark.parametrize("prec", TC_PRECS)
 @pytest.mark.parametrize("b", [8, 40, 72])
 def test_tensor_core_ring_matches_single_buffer(name, prec, b):
-    """The warp-specialised ring kernel (2, 3, 4 chunk stages) issues the same MMAs in the same
+    """The warp-specialised ring kernel (2, 3, 4 chunk stages: variants 20, 21, 22) issues the same MMAs in the same
     order as the single-buffer kernel: bit-identical results, and within the precision's bound
     of the oracle."""
     buf, info, P, op, ofo = get(name)
@@ -372,7 +372,7 @@ def test_tensor_core_ring_matches_single_buffer(name, prec, b):
         rc, y = _tc_apply(op, fn, xd, b, prec)
         assert rc == 0
         ref[w] = y.clone()
-    for var in (10, 11, 12):
+    for var in (20, 21, 22):
         op.set_variant(b, prec, var)
         for w, fn, oref in (("K", lib.fio_apply_K, fa.apply_Kdot), ("Kadj", lib.fio_apply_Kadj, fa.apply_Kdot_adj),
                             ("inv", lib.fio_apply_inv, fa.apply_inv)):
@@ -386,9 +386,10 @@ def test_tensor_core_ring_matches_single_buffer(name, prec, b):
 def test_set_variant_rejects_unknown_variants():
     buf, info, P, op, ofo = get("ex3_32")
     lib = binding.load()
-    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 9) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 11) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 9) == -1    # complex64-only tiles
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 8) == -1    # few-RHS kernel needs b <= 4
-    assert lib.fio_set_variant(op.h, 16, binding.FIO_PTF32, 3) == -1  # tensor-core launch: 0, 10-12
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_PTF32, 3) == -1  # tensor-core launch: 0, 20-22
     assert lib.fio_set_variant(op.h, 0, binding.FIO_P32, 1) == -1
     assert lib.fio_set_variant(op.h, 4, binding.FIO_P32, 8) == 0
     assert lib.fio_set_variant(op.h, 4, binding.FIO_P32, 0) == 0
