@@ -336,7 +336,8 @@ def main():
             "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
             "traffic": measured_traffic() if (a.n == 256 and b == 32 and a.kind == "ex3") else None,
             "traffic_unit": "DRAM bytes per apply (all stage launches), ncu",
-            "kernel": "k_stage_mm_pipe (every stage launch of one apply, float2, b=32)",
+            "kernel": "stage kernels k_stage_mm_vt / k_stage_mm_pipe (every stage launch of one apply, "
+                      "complex64, b=32, autotuned shapes)",
             "algorithmic_bytes_per_apply": int(kern_bytes),
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
             "hbm_view": {"achieved_gbs": round(kern_bytes / (kern_time / 1e3) / 1e9, 1),
