@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <type_traits>
 #include <new>
@@ -396,16 +397,34 @@ void launch_mm(StageArgs<V> a, cudaStream_t s) {
   k_stage_mm<V, ADJ, TX, TB, TR, ChunkK<V>::v><<<grid, 256, 0, s>>>(a);
 }
 
+// Dynamic shared memory above 48 KB is opted into per kernel and per device: remember, per (device,
+// kernel), the largest amount granted so far.  False when the attribute call fails (the launch
+// then fails and the call reports FIO_ECUDA, or the caller picks another variant).
+bool smem_opt_in(const void* func, int need) {
+  if (need <= 48 * 1024) return true;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> granted;
+  std::lock_guard<std::mutex> lock(mu);
+  int& cap = granted[std::make_pair(dev, func)];
+  if (need <= cap) return true;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, need) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cap = need;
+  return true;
+}
+
 template <typename V, bool ADJ, int TX, int TB, int TR>
 void launch_pipe(StageArgs<V> a, cudaStream_t s) {
   constexpr int CK = ChunkK<V>::v;
   using S = PipeShape<V, ADJ, TX, TB, TR, CK>;
-  static bool attr = false;  // one attribute call per instantiation (host-side, idempotent)
-  if (!attr) {
-    cudaFuncSetAttribute(k_stage_mm_pipe<V, ADJ, TX, TB, TR, CK>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-    attr = true;
-  }
+  smem_opt_in((const void*)k_stage_mm_pipe<V, ADJ, TX, TB, TR, CK>, S::SMEM);
   static_assert(S::RT == kTileRows, "tile lists are built for 64-row tiles");
   const int nrows = ADJ ? a.C : a.R;
   a.ntiles = (nrows + S::RT - 1) / S::RT;
@@ -419,11 +438,7 @@ void launch_pipe(StageArgs<V> a, cudaStream_t s) {
 template <bool ADJ, int TX, int TB, int TR, int NT>
 void launch_vt(StageArgs<float2> a, cudaStream_t s) {
   using S = VtShape<ADJ, TX, TB, TR, NT>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_stage_mm_vt<ADJ, TX, TB, TR, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-    attr = true;
-  }
+  smem_opt_in((const void*)k_stage_mm_vt<ADJ, TX, TB, TR, NT>, S::SMEM);
   static_assert(S::RT == kTileRows, "tile lists are built for 64-row tiles");
   const int nrows = ADJ ? a.C : a.R;
   a.ntiles = (nrows + S::RT - 1) / S::RT;
@@ -454,18 +469,10 @@ bool pipe_ok(const StageArgs<V>& a) {
 // the caller falls back to the tiled kernel)
 template <typename V, bool ADJ, int B>
 bool launch_vec_b(StageArgs<V> a, cudaStream_t s) {
-  static int cap = 48 * 1024;  // dynamic shared memory allowed so far for this instantiation
   const long long slots = (long long)(ADJ ? std::max<int>(a.R, 256) : a.C) * B;
   const long long need = slots * (long long)sizeof(V);
   if (need > 200 * 1024) return false;
-  if (need > cap) {
-    if (cudaFuncSetAttribute(k_stage_vec<V, ADJ, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    cap = (int)need;
-  }
+  if (!smem_opt_in((const void*)k_stage_vec<V, ADJ, B>, (int)need)) return false;
   const int nrows = ADJ ? a.C : a.R;
   a.ntiles = (nrows + kTileRows - 1) / kTileRows;
   const long long ncta = a.tiles ? a.ntiles_list : (long long)a.nblk * a.ntiles;
@@ -554,13 +561,8 @@ inline int tc_mode_of(int prec) {
 
 template <bool ADJ, int MODE>
 void launch_tc_dir(const TcArgs& a, int ncta, cudaStream_t s) {
-  static int cap = 48 * 1024;  // dynamic shared memory allowed without opting in
   const int need = tc_smem_bytes(MODE, a.nmax, a.ncmax);
-  if (need > cap) {
-    if (cudaFuncSetAttribute(k_stage_tc<ADJ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, need) ==
-        cudaSuccess)
-      cap = need;
-  }
+  smem_opt_in((const void*)k_stage_tc<ADJ, MODE>, need);
   dim3 grid((unsigned)ncta, (unsigned)((a.b + kTcMaxRhs - 1) / kTcMaxRhs));
   k_stage_tc<ADJ, MODE><<<grid, 128, need, s>>>(a);
 }
@@ -568,17 +570,9 @@ void launch_tc_dir(const TcArgs& a, int ncta, cudaStream_t s) {
 // the ring variant with S stages; false when its shared memory does not fit
 template <bool ADJ, int MODE, int S>
 bool launch_tc_ring(const TcArgs& a, int ncta, cudaStream_t s) {
-  static int cap = 48 * 1024;
   const int need = tc_ring_smem_bytes(MODE, a.nmax, a.ncmax, S);
   if (need > 227 * 1024) return false;
-  if (need > cap) {
-    if (cudaFuncSetAttribute(k_stage_tc_ring<ADJ, MODE, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, need) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    cap = need;
-  }
+  if (!smem_opt_in((const void*)k_stage_tc_ring<ADJ, MODE, S>, need)) return false;
   dim3 grid((unsigned)ncta, (unsigned)((a.b + kTcMaxRhs - 1) / kTcMaxRhs));
   k_stage_tc_ring<ADJ, MODE, S><<<grid, 192, need, s>>>(a);
   return true;

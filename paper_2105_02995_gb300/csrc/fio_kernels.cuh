@@ -40,6 +40,22 @@ __device__ __forceinline__ float2 cmac(float2 acc, float2 a, float2 b) {
   acc.y = fmaf(a.y, b.x, acc.y);
   return acc;
 }
+// acc += conj(a) * b, with the conjugation folded into the FMAs' operand signs (the same
+// operations, in the same order, as cmac(acc, cconj(a), b))
+__device__ __forceinline__ double2 cmacc(double2 acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 cmacc(float2 acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+  return acc;
+}
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 template <typename V> __device__ __forceinline__ V czero();
@@ -81,6 +97,7 @@ __device__ __forceinline__ dfc cmac(dfc acc, dfc a, dfc b) {
   return acc;
 }
 __device__ __forceinline__ dfc cconj(dfc a) { return dfc{a.rh, -a.ih, a.rl, -a.il}; }
+__device__ __forceinline__ dfc cmacc(dfc acc, dfc a, dfc b) { return cmac(acc, cconj(a), b); }
 template <> __device__ __forceinline__ dfc czero<dfc>() { return dfc{0.f, 0.f, 0.f, 0.f}; }
 // (s, c) -> double-float (hi, lo) with hi = fl(s + c) (Fast2Sum: |c| is below ulp-scale of |s|)
 __device__ __forceinline__ void df_norm(float s, float c, float& hi, float& lo) {
@@ -350,14 +367,13 @@ __global__ void __launch_bounds__(256) k_stage_mm_pipe(StageArgs<V> a) {
     for (int cc = 0; cc < CK; ++cc) {
       V m[TR], xv[TB];
 #pragma unroll
-      for (int i = 0; i < TR; ++i)
-        m[i] = ADJ ? cconj(tM[cc * MLD + ty + TY * i]) : tM[(ty + TY * i) * MLD + cc];
+      for (int i = 0; i < TR; ++i) m[i] = ADJ ? tM[cc * MLD + ty + TY * i] : tM[(ty + TY * i) * MLD + cc];
 #pragma unroll
       for (int q = 0; q < TB; ++q) xv[q] = tX[cc * BT + tx + TX * q];
 #pragma unroll
       for (int i = 0; i < TR; ++i)
 #pragma unroll
-        for (int q = 0; q < TB; ++q) acc[i][q] = cmac(acc[i][q], m[i], xv[q]);
+        for (int q = 0; q < TB; ++q) acc[i][q] = ADJ ? cmacc(acc[i][q], m[i], xv[q]) : cmac(acc[i][q], m[i], xv[q]);
     }
     __syncthreads();
   }
@@ -463,8 +479,8 @@ __global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
 #pragma unroll
         for (int i = 0; i < TR; i += 2) {
           const float4 v = *reinterpret_cast<const float4*>(tM + cc * MLD + ty * TR + i);
-          m[i] = make_float2(v.x, -v.y);
-          m[i + 1] = make_float2(v.z, -v.w);
+          m[i] = make_float2(v.x, v.y);
+          m[i + 1] = make_float2(v.z, v.w);
         }
       } else {
 #pragma unroll
@@ -479,7 +495,7 @@ __global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
 #pragma unroll
       for (int i = 0; i < TR; ++i)
 #pragma unroll
-        for (int q = 0; q < TB; ++q) acc[i][q] = cmac(acc[i][q], m[i], xv[q]);
+        for (int q = 0; q < TB; ++q) acc[i][q] = ADJ ? cmacc(acc[i][q], m[i], xv[q]) : cmac(acc[i][q], m[i], xv[q]);
     }
     __syncthreads();
   }
@@ -589,9 +605,9 @@ __global__ void __launch_bounds__(256) k_stage_vec(StageArgs<V> a) {
     for (int j = 0; j < B; ++j) acc[j] = czero<V>();
     if (cl < nc) {
       for (int r = g; r < ncols; r += G) {
-        const V m = cconj(M[(size_t)r * a.C + c]);
+        const V m = M[(size_t)r * a.C + c];
 #pragma unroll
-        for (int j = 0; j < B; ++j) acc[j] = cmac(acc[j], m, sX[j * ncols + r]);
+        for (int j = 0; j < B; ++j) acc[j] = cmacc(acc[j], m, sX[j * ncols + r]);
       }
     }
     __syncthreads();  // every thread is done with sX: reuse it for the partial sums
