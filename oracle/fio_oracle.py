@@ -29,6 +29,10 @@ Functions and their pins (tests/test_oracle.py):
   normal_matrix                           pinned: diag = N exactly, Hermitian positive definite,
                                           = N I for the linear phase
   cgne                                    pinned: agrees with solve_lu; true residual
+  F_matrix, apply_F, apply_Finv           the DFT f-hat = F f of section 1 (definition written out
+                                          densely; numpy.fft as the library DFT for large n)
+                                          pinned: dense definition vs numpy.fft, F^{-1} = the
+                                          linear-phase K (built from the phase formula), Parseval
 """
 
 from __future__ import annotations
@@ -256,3 +260,56 @@ def spectral_norm_est(apply, n: int, iters: int = 30, seed: int = 7) -> float:
             return 0.0
         x = y / lam
     return math.sqrt(lam)
+
+
+# ---- the DFT F of section 1: f-hat(xi) = n^{-d} sum_x exp(-2 pi i x.xi) f(x) ------------------
+
+def F_matrix(n: int, d: int) -> np.ndarray:
+    """Dense F (N x N, N = n^d): F[xi, x] = n^{-d} exp(-2 pi i x.xi), x.xi reduced exactly in
+    integers modulo n (same grids and 2D index i1 + n*i2 as K)."""
+    N = n ** d
+    k = np.arange(N)
+    if d == 1:
+        xi = k - n // 2
+        ip = np.outer(xi, k) % n                       # n * (x . xi) mod n, rows xi, cols x
+    else:
+        x1, x2 = k % n, k // n
+        xi1, xi2 = x1 - n // 2, x2 - n // 2
+        ip = (np.outer(xi1, x1) + np.outer(xi2, x2)) % n
+    return np.exp(-2j * np.pi * ip / n) / N
+
+
+def _modulation(n: int, d: int) -> np.ndarray:
+    """(-1)^(k_1 + ... + k_d): exp(-+2 pi i x.xi) with xi = j - n/2 splits into this sign times
+    the standard DFT kernel exp(-+2 pi i k.j / n)."""
+    k = np.arange(n ** d)
+    s = k % n if d == 1 else (k % n) + (k // n)
+    return np.where(s % 2 == 0, 1.0, -1.0)
+
+
+def apply_F(n: int, d: int, f: np.ndarray) -> np.ndarray:
+    """f-hat = F f for f of shape (N,) or (N, b), by numpy.fft (the library DFT)."""
+    f = np.asarray(f, dtype=complex)
+    vec = f.ndim == 1
+    f2 = f.reshape(f.shape[0], -1) * _modulation(n, d)[:, None]
+    if d == 1:
+        out = np.fft.fft(f2, axis=0) / n
+    else:
+        b = f2.shape[1]
+        out = (np.fft.fft2(f2.reshape(n, n, b), axes=(0, 1)) / (n * n)).reshape(n * n, b)
+    return out[:, 0] if vec else out
+
+
+def apply_Finv(n: int, d: int, fhat: np.ndarray) -> np.ndarray:
+    """f = F^{-1} f-hat: f(x) = sum_xi exp(2 pi i x.xi) f-hat(xi), by numpy.fft."""
+    g = np.asarray(fhat, dtype=complex)
+    vec = g.ndim == 1
+    g2 = g.reshape(g.shape[0], -1)
+    N = n ** d
+    if d == 1:
+        out = np.fft.ifft(g2, axis=0) * N
+    else:
+        b = g2.shape[1]
+        out = (np.fft.ifft2(g2.reshape(n, n, b), axes=(0, 1)) * N).reshape(N, b)
+    out = out * _modulation(n, d)[:, None]
+    return out[:, 0] if vec else out

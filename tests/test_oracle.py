@@ -163,3 +163,34 @@ def test_planted_sign_error_is_caught():
     f = np.arange(16) + 1j
     want = ((-1.0) ** np.arange(16)) * 16 * np.fft.ifft(f)
     assert fo.rel_err(K @ f, want) > 0.1
+
+
+@pytest.mark.parametrize("n,d", [(8, 1), (64, 1), (4, 2), (8, 2)])
+def test_dft_definition_vs_library(n, d):
+    """F written out from its definition (section 1) agrees with the numpy.fft path, in both
+    directions, for several right-hand sides."""
+    rng = np.random.default_rng(11)
+    N = n ** d
+    f = rng.standard_normal((N, 3)) + 1j * rng.standard_normal((N, 3))
+    F = fo.F_matrix(n, d)
+    assert fo.rel_err(fo.apply_F(n, d, f), F @ f) < 1e-13
+    assert fo.rel_err(fo.apply_Finv(n, d, F @ f), f) < 1e-13
+    assert fo.rel_err(fo.apply_Finv(n, d, f), np.linalg.solve(F, f)) < 1e-12
+
+
+@pytest.mark.parametrize("kind,n", [("linear1d", 32), ("linear2d", 8)])
+def test_Finv_is_the_linear_phase_K(kind, n):
+    """F^{-1} is the FIO with Phi = x.xi and a = 1 (K built from the phase formula)."""
+    op = fo.FIO(kind, n)
+    rng = np.random.default_rng(12)
+    g = rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)
+    assert fo.rel_err(fo.apply_Finv(n, op.d, g), fo.dense_K(op) @ g) < 1e-13
+
+
+def test_dft_parseval():
+    """||F f||^2 = n^-d ||f||^2 (F is n^{-d/2} times a unitary matrix)."""
+    rng = np.random.default_rng(13)
+    for n, d in ((64, 1), (16, 2)):
+        f = rng.standard_normal(n ** d) + 1j * rng.standard_normal(n ** d)
+        lhs = np.linalg.norm(fo.apply_F(n, d, f)) ** 2
+        assert abs(lhs - np.linalg.norm(f) ** 2 / n ** d) < 1e-12 * lhs
