@@ -379,6 +379,37 @@ def main():
         except Exception as exc:  # reported, not hidden: the variant line says why it is missing
             variants[name] = {"error": str(exc)[:200]}
 
+    # full solve of u = K F f (section 1): f = F^{-1} G K* u, complex64; and the inverse DFT alone
+    # (two shared-memory FFT passes, each reading and writing the N x b vector: HBM-bound)
+    try:
+        fsol = binding.colmajor(torch.empty_like(u))
+        for _ in range(3):
+            op.apply_inv(u, f)
+            op.apply_Finv(f, fsol)
+        torch.cuda.synchronize()
+        evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        for k in range(a.steps):
+            flush.fill_(float(k))
+            evf[k][0].record(stream)
+            op.apply_inv(u, f)
+            evf[k][1].record(stream)
+            op.apply_Finv(f, fsol)
+            evf[k][2].record(stream)
+        torch.cuda.synchronize()
+        full_ms = allmax(ws, statistics.mean(e0.elapsed_time(e2) for e0, _, e2 in evf))
+        finv_ms = statistics.mean(e1.elapsed_time(e2) for _, e1, e2 in evf)
+        npass = 2 if (info.get("d", 2) == 2 or N > 2048) else 1
+        finv_bytes = npass * 2 * 8 * N * b
+        peak_hbm = measured_peaks()[0].get("hbm_gbs")
+        variants["full_solve_u_eq_KFf"] = {
+            "value": round(ws * b * 1000.0 / full_ms, 2), "unit": "RHS/s", "ms_per_step": round(full_ms, 4),
+            "Finv_ms": round(finv_ms, 4), "Finv_gbs": round(finv_bytes / finv_ms / 1e6, 1),
+            "Finv_frac_of_hbm": round(finv_bytes / finv_ms / 1e6 / peak_hbm, 3) if peak_hbm else None,
+            "Finv_bytes_per_apply": finv_bytes}
+    except Exception as exc:
+        variants["full_solve_u_eq_KFf"] = {"error": str(exc)[:200]}
+
     # solve latency to ||u - K-dot f|| <= 1e-10 ||u||: the plain FP64 path (PCG on K*K with G, FP64
     # factors, one right-hand side per call) against FP64-residual iterative refinement whose
     # corrections run on the tensor cores, on batches of b right-hand sides

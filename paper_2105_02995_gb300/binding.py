@@ -25,6 +25,7 @@ FIO_MASK_P64, FIO_MASK_P32, FIO_MASK_TC, FIO_MASK_DF = 1, 2, 4, 8
 STATUS = {0: "FIO_OK", -1: "FIO_EINVAL", -2: "FIO_ENOMEM", -3: "FIO_EBADFACTORS",
           -4: "FIO_ENOCONV", -5: "FIO_ETIMEOUT", -6: "FIO_ECUDA", -7: "FIO_ENOTSUP"}
 SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv",
+           "fio_apply_F", "fio_apply_Finv",
            "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_apply_profiled",
            "fio_apply_inv_noalloc", "fio_selftest_wait", "fio_autotune", "fio_set_variant", "fio_release",
            "fio_strerror"]
@@ -58,7 +59,7 @@ def load(path: str = LIB_PATH):
     vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
     lib.fio_upload_factors.argtypes = [vp, ctypes.c_size_t, ctypes.c_uint, vp, ctypes.POINTER(vp)]
     for name in ("fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv", "fio_apply_inv_host",
-                 "fio_apply_inv_noalloc"):
+                 "fio_apply_inv_noalloc", "fio_apply_F", "fio_apply_Finv"):
         getattr(lib, name).argtypes = [vp, vp, vp, i64, c_int, c_int, c_int, vp]
     lib.fio_solve.argtypes = [vp, vp, vp, i64, c_int, c_int, ctypes.POINTER(SolveOpts),
                               ctypes.POINTER(SolveInfo), vp]
@@ -192,6 +193,14 @@ class Operator:
 
     def apply_G(self, x, y=None, precision=None):
         return self._apply(self._lib.fio_apply_G, "fio_apply_G", x, y, precision)
+
+    def apply_F(self, f, fhat=None):
+        """f-hat = F f, the DFT of section 1 (fio_apply_F)."""
+        return self._apply(self._lib.fio_apply_F, "fio_apply_F", f, fhat)
+
+    def apply_Finv(self, fhat, f=None):
+        """f = F^{-1} f-hat (fio_apply_Finv): with apply_inv, the full solve of u = K F f."""
+        return self._apply(self._lib.fio_apply_Finv, "fio_apply_Finv", fhat, f)
 
     def apply_inv(self, u, f=None, precision=None):
         """f = G-dot K-dot* u; precision defaults to the dtype's (P64 / P32), or FIO_PTF32 /
