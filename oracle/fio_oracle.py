@@ -13,6 +13,12 @@ What it follows (paper section and equation; the paper numbers equations per sec
     c1 = (2 + sin 2pi x1 sin 2pi x2)/16, c2 = (2 + cos 2pi x1 cos 2pi x2)/16.
   * "linear": Phi = x.xi, a = 1 (Example 1 with c = 0).  Then K is diag((-1)^i) times the
     unnormalised inverse DFT (closed form used as a pin).
+  * Example 2 (section 6): the phase of Example 1 with a variable amplitude, a mixture of
+    Gaussians sum_k exp(-((x - x_k)^2 + (xi - xi_k)^2) / sigma^2), periodic in x on [0, 1],
+    sigma^2 = 0.1 ("ex2a") or 0.05 ("ex2b").  The paper gives neither the number of terms nor
+    the centres nor the scale of xi; the reading here: four terms, centres
+    (x_k, eta_k) = ((2k+1)/8, (2k-3)/8), k = 0..3, with xi measured as eta = xi/N in [-1/2, 1/2)
+    and x - x_k as the periodic distance in [-1/2, 1/2).
 
 Readings where the paper is silent:
   * 2D linear index: point (i1, i2) has index i1 + n*i2, for X and for Omega alike.
@@ -43,7 +49,9 @@ from dataclasses import dataclass
 import numpy as np
 import scipy.linalg
 
-KINDS = ("ex1", "ex3", "linear1d", "linear2d")
+KINDS = ("ex1", "ex2a", "ex2b", "ex3", "linear1d", "linear2d")
+EX2_SIGMA2 = {"ex2a": 0.1, "ex2b": 0.05}
+EX2_CENTRES = [((2 * k + 1) / 8.0, (2 * k - 3) / 8.0) for k in range(4)]
 
 
 @dataclass(frozen=True)
@@ -55,7 +63,7 @@ class FIO:
 
     @property
     def d(self) -> int:
-        return 1 if self.kind in ("ex1", "linear1d") else 2
+        return 1 if self.kind in ("ex1", "ex2a", "ex2b", "linear1d") else 2
 
     @property
     def N(self) -> int:
@@ -90,7 +98,7 @@ def phase_frac(op: FIO, rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
         num += np.outer(kx[:, t], xi[:, t])
     lin = np.mod(num, n).astype(np.float64) / n
     x = kx.astype(np.float64) / n
-    if op.kind == "ex1":
+    if op.kind in ("ex1", "ex2a", "ex2b"):
         c = (2.0 + np.sin(2.0 * np.pi * x[:, 0])) / 8.0
         smooth = np.outer(c, np.abs(xi[:, 0]).astype(np.float64))
     elif op.kind == "ex3":
@@ -110,10 +118,27 @@ def phase_frac(op: FIO, rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
     return theta - np.round(theta)
 
 
+def amplitude(op: FIO, rows, cols) -> np.ndarray:
+    """a(x_rows, xi_cols): 1 except for Example 2 (the Gaussian mixture of the module docstring)."""
+    rows, cols = np.asarray(rows), np.asarray(cols)
+    if op.kind not in EX2_SIGMA2:
+        return np.ones((len(rows), len(cols)))
+    kx, _ = grid(op, rows)
+    _, xi = grid(op, cols)
+    x = kx[:, 0].astype(np.float64) / op.n
+    eta = xi[:, 0].astype(np.float64) / op.N
+    s2 = EX2_SIGMA2[op.kind]
+    a = np.zeros((len(rows), len(cols)))
+    for xk, ek in EX2_CENTRES:
+        dx = (x - xk + 0.5) % 1.0 - 0.5          # periodic distance in x
+        a += np.outer(np.exp(-dx * dx / s2), np.exp(-(eta - ek) ** 2 / s2))
+    return a
+
+
 def K_block(op: FIO, rows, cols) -> np.ndarray:
-    """Entries K[rows, cols] = a exp(2 pi i Phi) with a = 1 (eq. 1.3)."""
+    """Entries K[rows, cols] = a exp(2 pi i Phi) (eq. 1.3)."""
     theta = phase_frac(op, np.asarray(rows), np.asarray(cols))
-    return np.exp(2j * np.pi * theta)
+    return amplitude(op, rows, cols) * np.exp(2j * np.pi * theta)
 
 
 def dense_K(op: FIO) -> np.ndarray:

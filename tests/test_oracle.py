@@ -194,3 +194,47 @@ def test_dft_parseval():
         f = rng.standard_normal(n ** d) + 1j * rng.standard_normal(n ** d)
         lhs = np.linalg.norm(fo.apply_F(n, d, f)) ** 2
         assert abs(lhs - np.linalg.norm(f) ** 2 / n ** d) < 1e-12 * lhs
+
+
+def test_ex2_amplitude_golden():
+    """Example 2's amplitude at hand-worked points (tests/golden/ex2_amplitude.txt): periodic
+    distance in x, xi scaled by N, the four centres, sigma^2 of the paper's two tables."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "ex2_amplitude.txt")
+    sigma2 = {"ex2a": 0.1, "ex2b": 0.05}
+    n_rows = 0
+    with open(path) as fh:
+        for line in fh:
+            if not line.strip() or line.startswith("#"):
+                continue
+            kind, n, r, c, *q = line.split()
+            want = sum(np.exp(-(int(v) / 64.0) / sigma2[kind]) for v in q)
+            got = fo.amplitude(fo.FIO(kind, int(n)), [int(r)], [int(c)])[0, 0]
+            assert abs(got - want) < 1e-14 * want, (kind, r, c, got, want)
+            n_rows += 1
+    assert n_rows == 6
+
+
+@pytest.mark.parametrize("kind", ["ex2a", "ex2b"])
+def test_ex2_is_ex1_times_amplitude(kind):
+    """|K_ij| = a(x_i, xi_j) > 0 and K / |K| is Example 1's K: the amplitude changes the modulus only."""
+    op, op1 = fo.FIO(kind, 64), fo.FIO("ex1", 64)
+    K, K1 = fo.dense_K(op), fo.dense_K(op1)
+    a = fo.amplitude(op, np.arange(64), np.arange(64))
+    assert a.min() > 0
+    assert np.max(np.abs(np.abs(K) - a)) < 1e-14
+    assert np.max(np.abs(K / np.abs(K) - K1)) < 1e-13
+
+
+def test_ex2_normal_matrix_hpd_and_harder():
+    """K*K stays Hermitian positive definite, and the narrower amplitude (sigma^2 = 0.05) is worse
+    conditioned than the wider one, which is worse than Example 1 (the effect the paper's Example 2
+    tables show through the iteration counts of CG with K* alone)."""
+    conds = {}
+    for kind in ("ex1", "ex2a", "ex2b"):
+        op = fo.FIO(kind, 128)
+        S = fo.normal_matrix(op)
+        assert np.max(np.abs(S - S.conj().T)) < 1e-9
+        ev = np.linalg.eigvalsh(S)
+        assert ev.min() > 0
+        conds[kind] = ev.max() / ev.min()
+    assert conds["ex1"] < conds["ex2a"] < conds["ex2b"], conds
