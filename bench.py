@@ -161,10 +161,28 @@ def get_operator(a, rank, ws):
     return buf, info
 
 
+OPERATORS = {"ex3": "2D generalized Radon transform (Example 3)", "ex1": "1D FIO (Example 1)",
+             "ex2a": "1D FIO with variable amplitude, sigma^2 = 0.1 (Example 2)",
+             "ex2b": "1D FIO with variable amplitude, sigma^2 = 0.05 (Example 2)"}
+
+
+def grid_size(a):
+    return a.n * a.n if a.kind == "ex3" else a.n
+
+
+def metric_of(a):
+    """The headline metric's name (2D n = 256 by default; other operators name themselves)."""
+    if a.kind == "ex3":
+        return f"inverse-apply RHS/s at 2D n={a.n}"
+    return f"inverse-apply RHS/s at {a.kind} N={a.n}"
+
+
 def config_of(a, info, l2):
-    return {"workload": f"2D generalized Radon transform (Example 3), n={a.n} (N={a.n * a.n}), direct "
+    N = grid_size(a)
+    size = f"n={a.n} (N={N})" if a.kind == "ex3" else f"N={N}"
+    return {"workload": f"{OPERATORS.get(a.kind, a.kind)}, {size}, direct "
                         f"inverse apply f = G K* u, complex64 (FP32 arithmetic), b={a.b} RHS per step",
-            "kind": a.kind, "n": a.n, "N": a.n * a.n, "b": a.b, "eps_bf": a.eps_bf, "eps_hif": a.eps_hif,
+            "kind": a.kind, "n": a.n, "N": N, "b": a.b, "eps_bf": a.eps_bf, "eps_hif": a.eps_hif,
             "L": info.get("L"), "LH": info.get("LH"), "root": info.get("root"), "l2": l2,
             "parallelism": "replicas"}
 
@@ -192,7 +210,7 @@ def run_reference(a, ws, rank):
     import numpy as np
     from paper_2105_02995_gb300.inputs import complex_gaussian, rhs_seed
     buf, info = get_operator(a, 0, 1)
-    u = complex_gaussian(a.n * a.n, a.b, rhs_seed(2))
+    u = complex_gaussian(grid_size(a), a.b, rhs_seed(2))
     from oracle import factor_apply as fa
     P = fa.PackedFactors(buf, verify=False)
     for _ in range(a.warmup):
@@ -204,7 +222,7 @@ def run_reference(a, ws, rank):
         times.append(time.perf_counter() - s)
     ms = 1000 * statistics.mean(times)
     val = 1000.0 / ms
-    line = {"metric": "inverse-apply RHS/s at 2D n=256", "value": val, "unit": "RHS/s", "n_gpus": ws,
+    line = {"metric": metric_of(a), "value": val, "unit": "RHS/s", "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": config_of(a, info, "host only"),
@@ -489,7 +507,7 @@ def main():
         cpu = cpu_baseline(buf, a, u_np)
     launches = op.launches("inv", b) * a.steps
     if rank == 0:
-        line = {"metric": "inverse-apply RHS/s at 2D n=256", "value": round(value, 2), "unit": "RHS/s",
+        line = {"metric": metric_of(a), "value": round(value, 2), "unit": "RHS/s",
                 "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": config_of(a, info, "flushed before every step (256 MB write)"),

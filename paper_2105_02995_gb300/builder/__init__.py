@@ -17,7 +17,7 @@ from .hmatrix import HGeometry, peel
 from .pack import pack
 from .stages import KIND_MAP
 
-DIMS = {"ex1": 1, "linear1d": 1, "ex3": 2, "linear2d": 2}
+DIMS = {"ex1": 1, "ex2a": 1, "ex2b": 1, "linear1d": 1, "ex3": 2, "linear2d": 2}
 
 
 class PaddedStages:

@@ -27,6 +27,7 @@ def spec(A):
 
 
 @pytest.mark.parametrize("kind,n,L,eps", [("ex1", 256, 4, 1e-6), ("ex1", 1024, 6, 1e-9),
+                                          ("ex2a", 256, 4, 1e-7), ("ex2b", 256, 4, 1e-7),
                                           ("ex3", 16, 2, 1e-4), ("ex3", 32, 3, 1e-6)])
 def test_butterfly_error(kind, n, L, eps):
     """e_a of the butterfly within a small multiple of its tolerance (section 2, eq. for K-dot)."""
@@ -38,10 +39,14 @@ def test_butterfly_error(kind, n, L, eps):
 
 
 @pytest.mark.parametrize("kind,n,eb,eh,bound", [("ex1", 256, 1e-7, 1e-6, 2e-5), ("ex1", 1024, 1e-7, 1e-6, 5e-5),
-                                                ("ex1", 256, 1e-4, 1e-3, 2e-2), ("ex3", 32, 1e-5, 1e-3, 2e-2)])
+                                                ("ex1", 256, 1e-4, 1e-3, 2e-2), ("ex3", 32, 1e-5, 1e-3, 2e-2),
+                                                ("ex2a", 256, 1e-7, 1e-6, 1e-3), ("ex2b", 256, 1e-7, 1e-6, 1e-2)])
 def test_inverse_error_es(kind, n, eb, eh, bound):
     """e_s = ||I - G-dot K-dot* K|| of the packed operator (the paper reports e_s of the order of
-    eps to 10 eps at these sizes, Tables for Examples 1 and 3)."""
+    eps to 10 eps at these sizes, Tables for Examples 1 and 3).  With Example 2's amplitude K*K is
+    worse conditioned (cond(K) 17 and 112 at N = 1024 for sigma^2 = 0.1 and 0.05, against 3 for
+    Example 1) and e_s grows with it, as in the paper's Example 2 tables (e_s up to 3e-3 at
+    eps = 1e-4 for sigma^2 = 0.05): bounds 1e-3 and 1e-2."""
     buf, info = built(kind, n, eb, eh)
     P = fa.PackedFactors(buf)
     op = fo.FIO(kind, n)
