@@ -228,10 +228,13 @@ def test_refinement_with_tensor_core_inner(prec):
 
 
 # Double-float (FIO_PDF): every factor entry and vector value as hi + lo floats (48-bit
-# significand, unit roundoff 2^-49 ~ 1.8e-15) with compensated accumulation (sums as if in twice
-# the working precision): per stage a few units of 2^-48 relative, over ~20 stages and sums of
-# ~300 terms well inside TOL64 = 1e-12, the bound of the FP64 path.  A kernel that lost the low
-# parts anywhere would land at the FP32 error (~1e-7).
+# significand) with compensated accumulation (Dot2: error ~ u|s| + (n u)^2 sum|terms| with the
+# working precision u = 2^-24, against ~ n u64 sum|terms| for FP64 FMA chains, u64 = 2^-53).
+# Both paths' errors are amplified alike by the conditioning of the products (the HIF factors of
+# an ill-conditioned K*K, Example 2), so the bound follows the FP64 path's own error on the same
+# factors: the typical (random-walk) ratio of the two is u^2 / u64 = 2^5, the worst-case ratio
+# n u^2 / u64 = n 2^5 (n <= ~300 terms per sum); the bound takes 2^8 times the FP64 error, and at
+# least TOL64.  A kernel that lost the low parts anywhere would land at the FP32 error (~1e-7).
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("b", [1, 3, 8, 37])
 def test_apply_double_float_vs_factor_oracle(name, b):
@@ -240,9 +243,12 @@ def test_apply_double_float_vs_factor_oracle(name, b):
     xd = dev(x)
     for what, ref in (("K", fa.apply_Kdot), ("Kadj", fa.apply_Kdot_adj), ("G", fa.apply_G),
                       ("inv", fa.apply_inv)):
+        want = ref(P, x)
+        y64 = getattr(op, "apply_" + what)(xd)
         y = getattr(op, "apply_" + what)(xd, precision=binding.FIO_PDF)
         torch.cuda.synchronize()
-        assert rel(host(y), ref(P, x)) < TOL64, what
+        e64 = rel(host(y64), want)
+        assert rel(host(y), want) < max(TOL64, 256 * e64), (what, e64)
 
 
 def test_double_float_precision_pairs():
