@@ -67,11 +67,13 @@ def default_levels(kind: str, n: int):
 
 
 def build_operator(kind: str, n: int, eps_bf: float, eps_hif: float, L: int = None,
-                   LH: int = None, mv=None, seed: int = 20210506, verbose: bool = False):
+                   LH: int = None, mv=None, seed: int = 20210506, verbose: bool = False,
+                   hif_rescale: bool = False):
     """Algorithm 1: K-dot <- BFF(eps_bf); S-dot <- peeling(K-dot, eps_hif); G-dot <- HIF(S-dot, eps_hif).
 
     mv(X) may supply K-dot* K-dot X (e.g. on the GPU); by default the builder's own numpy product
-    of the butterfly stages is used.  Returns (packed bytes, info dict).
+    of the butterfly stages is used.  hif_rescale selects the Cholesky-rescaled skeletonization
+    (section 4.1) for the HIF.  Returns (packed bytes, info dict).
     """
     d = DIMS[kind]
     L0, LH0 = default_levels(kind, n)
@@ -97,12 +99,13 @@ def build_operator(kind: str, n: int, eps_bf: float, eps_hif: float, L: int = No
     # own U-bar removes few DOFs; accept columns below eps ||A|| as well (the error that matters
     # for the inverse).  1D keeps the node-relative criterion.
     hif_stages, hif = build_hif(H, eps_hif, verbose=verbose,
-                                tol_mode="global" if d == 2 else "local")
+                                tol_mode="global" if d == 2 else "local", rescale=hif_rescale)
     t3 = time.time()
     if verbose:
         print(f"[build] HIF: {t3 - t2:.1f} s, root {hif.root_size}, steps {hif.stats}", flush=True)
     buf = pack(d, n, bf, hif_stages[:-1], hif_stages[-1:], eps_bf, eps_hif, flags=(d == 2))
     info = dict(kind=kind, n=n, d=d, N=n ** d, L=L, LH=LH, eps_bf=eps_bf, eps_hif=eps_hif,
+                hif_rescale=hif_rescale,
                 t_bf=t1 - t0, t_peel=t2 - t1, t_hif=t3 - t2, root=hif.root_size,
                 nnz_bf=sum(s.nnz for s in bf), nnz_hif=sum(s.nnz for s in hif_stages),
                 bf_shapes=[s.padded_shape() for s in bf],

@@ -39,9 +39,9 @@ def cache_dir() -> str:
     return d
 
 
-def build_cached(kind, n, eps_bf, eps_hif, gpu=False, threads=None, verbose=True):
+def build_cached(kind, n, eps_bf, eps_hif, gpu=False, threads=None, verbose=True, hif_rescale=False):
     """Build (or reuse) an operator in a subprocess with single-threaded BLAS; returns (bytes, info)."""
-    key = f"{kind}_{n}_{eps_bf:g}_{eps_hif:g}_{source_hash()}"
+    key = f"{kind}_{n}_{eps_bf:g}_{eps_hif:g}{'_resc' if hif_rescale else ''}_{source_hash()}"
     path = os.path.join(cache_dir(), key + ".fio")
     meta = path + ".json"
     if not (os.path.exists(path) and os.path.exists(meta)):
@@ -52,6 +52,8 @@ def build_cached(kind, n, eps_bf, eps_hif, gpu=False, threads=None, verbose=True
                "--eps-bf", repr(eps_bf), "--eps-hif", repr(eps_hif), "--out", path]
         if gpu:
             cmd.append("--gpu")
+        if hif_rescale:
+            cmd.append("--hif-rescale")
         # the build's progress goes to stderr: stdout of the caller stays free for its own output
         out = sys.stderr if verbose else subprocess.PIPE
         r = subprocess.run(cmd, env=env, stdout=out, stderr=out, text=True)
@@ -72,6 +74,7 @@ def main(argv=None):
     ap.add_argument("--eps-hif", type=float, required=True)
     ap.add_argument("--out", required=True)
     ap.add_argument("--gpu", action="store_true")
+    ap.add_argument("--hif-rescale", action="store_true", help="Cholesky-rescaled HIF skeletonization")
     a = ap.parse_args(argv)
     sys.path.insert(0, ROOT)
     from paper_2105_02995_gb300.builder import build_operator
@@ -82,7 +85,7 @@ def main(argv=None):
         prec = binding.FIO_P32 if a.eps_hif >= 1e-4 else binding.FIO_P64
         mv = binding.NormalMatvecGPU(prec)
     t = time.time()
-    buf, info = build_operator(a.kind, a.n, a.eps_bf, a.eps_hif, mv=mv, verbose=True)
+    buf, info = build_operator(a.kind, a.n, a.eps_bf, a.eps_hif, mv=mv, verbose=True, hif_rescale=a.hif_rescale)
     info["t_total"] = time.time() - t
     info["peel_on_gpu"] = bool(a.gpu)
     tmp = a.out + ".tmp"

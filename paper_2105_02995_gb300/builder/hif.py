@@ -18,6 +18,14 @@ Finally A_0, the matrix on the remaining active DOFs, is formed densely and inve
 
 Every node contributes the dense matrix (Z_I E_I)* on its index set, ordered (I~, I^):
         (Z E)* = [[L^{-1}, -L^{-1} T*], [-W, I + W T*]],
+In general the zeroing is the change of basis x_I = V y~ + P^ y^ whose redundant columns
+V span the directions the ID declares decoupled from the rest of the matrix: V = P~ - P^ T for
+the ID above, and V = C^{-*} (P~ - P^ T') for the Cholesky-rescaled variant of section 4.1
+(rescale=True): A_II = C C*, and the ID is taken on the scaled U-bar C^{-*}, so that the block
+to eliminate, V* A V = I + T'* T', is well conditioned whatever A_II is (the variant the paper
+recommends for ill-conditioned matrices).  The skeleton keeps its columns P^ in both, so the
+outside couples to the same DOFs and the rest of the algorithm is unchanged.  Node factor:
+        (Z E)* = [[L^{-1} V*], [P^* - W V*]],  V* A V = L L*,  W = (P^* A V) (V* A V)^{-1},
 one INPLACE block of the stage R_l* (or Rbar_l*); the root stage holds A_0^{-1}.  Then
         G-dot = R_L ... R_1 A_0^{-1} R_1* ... R_L*   (1D, eq. for G-dot)
 and the 2D product with Rbar_l between the cell factors (eq. for G-dot in 2D).
@@ -104,9 +112,45 @@ def eliminate(A: np.ndarray, red: np.ndarray, skel: np.ndarray, T: np.ndarray):
     return M, schur
 
 
+def rescaled_skeletonize(A: np.ndarray, Ub: np.ndarray, eps: float):
+    """The Cholesky-rescaled skeletonization of one node (section 4.1): ID of U-bar C^{-*} with
+    A = C C*, redundant basis V = C^{-*} (P~ - P^ T'), then the elimination of V* A V.
+
+    Returns (red, skel, M, schur) like interp_decomp + eliminate, or (red, skel, None, None)
+    when nothing is redundant."""
+    n = A.shape[0]
+    Ah = 0.5 * (A + A.conj().T)
+    Cinv, _ = hpd_factor(Ah)                     # C^{-1} for A = C C* (any square root)
+    CinvH = Cinv.conj().T                        # C^{-*}
+    skel, red, T = interp_decomp(Ub @ CinvH, eps, n)
+    if len(red) == 0:
+        return red, skel, None, None
+    nr, ns = len(red), len(skel)
+    Y = np.zeros((n, nr), dtype=np.complex128)   # P~ - P^ T'
+    Y[red, np.arange(nr)] = 1.0
+    Y[skel, :] -= T
+    V = CinvH @ Y
+    AV = Ah @ V
+    Arr_t = V.conj().T @ AV
+    Arr_t = 0.5 * (Arr_t + Arr_t.conj().T)
+    Asr_t = AV[skel, :]
+    Linv, Arr_inv = hpd_factor(Arr_t)
+    W = Asr_t @ Arr_inv
+    schur = Ah[np.ix_(skel, skel)] - W @ Asr_t.conj().T
+    schur = 0.5 * (schur + schur.conj().T)
+    order = np.concatenate([red, skel])
+    VH = V.conj().T[:, order]                    # V* in (red, skel) column order
+    Ps = np.zeros((ns, n), dtype=np.complex128)
+    Ps[np.arange(ns), skel] = 1.0
+    M = np.empty((n, n), dtype=np.complex128)
+    M[:nr] = Linv @ VH
+    M[nr:] = Ps[:, order] - W @ VH
+    return red, skel, M, schur
+
+
 class HIF:
     def __init__(self, H: HMatrix, eps: float, edges: bool = None, stop_level: int = None,
-                 tol_mode: str = "local"):
+                 tol_mode: str = "local", rescale: bool = False):
         self.H = H
         self.g = H.geom
         self.t = self.g.tree
@@ -119,6 +163,9 @@ class HIF:
         # "local": relative to each node's U-bar (the paper's ID accuracy statement);
         # "global": also accept columns whose residual is below eps ||A||_2
         self.abs_tol = eps * H.normA if tol_mode == "global" else 0.0
+        # Cholesky-rescaled skeletonization (section 4.1); its ID is relative to the scaled
+        # U-bar, whose block against the node itself is the identity
+        self.rescale = rescale
         self.stages = []
         self.stats = []
         self._far_factors()
@@ -205,6 +252,9 @@ class HIF:
             rows = [self.near[(c2, c)] for c2 in g.NL[lvl][c] if c2 != c]
             rows += self._far_rows(lvl, c, I)
             Ub = np.vstack(rows) if rows else np.zeros((0, len(I)))
+            if self.rescale:
+                red, skel, M, schur = rescaled_skeletonize(self.near[(c, c)], Ub, self.eps)
+                return c, ((red, skel, M, schur) if len(red) else None)
             skel, red, T = interp_decomp(Ub, self.eps, len(I), self.abs_tol)
             if len(red) == 0:
                 return c, None
@@ -309,15 +359,20 @@ class HIF:
                         blk[:, nI1:] = F
                     rows.append(blk)
             Ub = np.vstack(rows) if rows else np.zeros((0, nI))
-            skel, red, T = interp_decomp(Ub, self.eps, nI, self.abs_tol)
-            if len(red) == 0:
-                return None
             A = np.empty((nI, nI), dtype=np.complex128)
             A[:nI1, :nI1] = self.near[(c1, c1)][np.ix_(p1, p1)]
             A[nI1:, nI1:] = self.near[(c2, c2)][np.ix_(p2, p2)]
             A[:nI1, nI1:] = self.near[(c1, c2)][np.ix_(p1, p2)]
             A[nI1:, :nI1] = self.near[(c2, c1)][np.ix_(p2, p1)]
-            M, schur = eliminate(A, red, skel, T)
+            if self.rescale:
+                red, skel, M, schur = rescaled_skeletonize(A, Ub, self.eps)
+                if len(red) == 0:
+                    return None
+            else:
+                skel, red, T = interp_decomp(Ub, self.eps, nI, self.abs_tol)
+                if len(red) == 0:
+                    return None
+                M, schur = eliminate(A, red, skel, T)
             I = np.concatenate([I1, I2])
             return (c1, c2, I, nI1, red, skel, M, schur)
 

@@ -123,3 +123,62 @@ def test_butterfly_sampled_path_large_N():
     got = ps.apply(f)[rows]
     want = fo.K_rows(fo.FIO("ex1", N), rows, f)
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 5 * eps
+
+
+def _node_check(A, nI, M, red, skel, schur):
+    """Apply R* = blockdiag(M, I) (M on the node's DOFs in (red, skel) order) to the whole HPD A:
+    the redundant block must become the identity and decouple from everything else, and the
+    skeleton block must be the returned Schur complement."""
+    n = A.shape[0]
+    order = np.concatenate([red, skel, np.arange(nI, n)])
+    Ap = A[np.ix_(order, order)]
+    Rs = np.eye(n, dtype=complex)
+    Rs[:nI, :nI] = M
+    B = Rs @ Ap @ Rs.conj().T
+    nr, ns = len(red), len(skel)
+    scale = np.linalg.norm(A, 2)
+    assert np.linalg.norm(B[:nr, :nr] - np.eye(nr)) < 1e-10
+    assert np.linalg.norm(B[:nr, nr:]) < 1e-9 * scale
+    assert np.linalg.norm(B[nr:nr + ns, nr:nr + ns] - schur) < 1e-9 * scale
+
+
+@pytest.mark.parametrize("rescale", [False, True])
+def test_node_factor_decouples_redundant_dofs(rescale):
+    """One skeletonization step (section 4.1) on an HPD matrix whose node-to-rest coupling has
+    exact rank 3 and whose node block is ill-conditioned (cond ~ 1e6): both the plain ID +
+    elimination and the Cholesky-rescaled variant make the redundant block the identity and
+    decouple it exactly."""
+    from paper_2105_02995_gb300.builder.hif import eliminate, interp_decomp, rescaled_skeletonize
+    rng = np.random.default_rng(21)
+    nI, nB, r = 12, 20, 3
+    Q, _ = np.linalg.qr(rng.standard_normal((nI, nI)) + 1j * rng.standard_normal((nI, nI)))
+    AII = (Q * np.logspace(0, -6, nI)) @ Q.conj().T * 50 + 1e-3 * np.eye(nI)
+    U = rng.standard_normal((nB, r)) + 1j * rng.standard_normal((nB, r))
+    Vt = rng.standard_normal((r, nI)) + 1j * rng.standard_normal((r, nI))
+    ABI = 1e-3 * U @ Vt
+    ABB = 10 * np.eye(nB) + 0.1 * (lambda X: X @ X.conj().T)(rng.standard_normal((nB, nB)))
+    A = np.block([[AII, ABI.conj().T], [ABI, ABB]])
+    assert np.linalg.eigvalsh(A).min() > 0
+    if rescale:
+        red, skel, M, schur = rescaled_skeletonize(AII, ABI, 1e-12)
+    else:
+        skel, red, T = interp_decomp(ABI, 1e-12, nI)
+        M, schur = eliminate(AII, red, skel, T)
+    assert len(skel) == r and len(red) == nI - r
+    _node_check(A, nI, M, red, skel, schur)
+
+
+def test_rescaled_hif_accuracy():
+    """The Cholesky-rescaled HIF (section 4.1) reaches the standard variant's e_s bounds: Example 1,
+    Example 2 (sigma^2 = 0.1) and Example 3; and it reproduces G-dot = I/N exactly for the linear
+    phase (K*K = N I: every DOF decouples at the leaves)."""
+    for kind, n, eb, eh, bound in (("ex1", 256, 1e-7, 1e-6, 2e-5), ("ex2a", 256, 1e-7, 1e-6, 1e-3),
+                                   ("ex3", 32, 1e-5, 1e-3, 2e-2)):
+        buf, _ = build_operator(kind, n, eb, eh, hif_rescale=True)
+        P = fa.PackedFactors(buf)
+        op = fo.FIO(kind, n)
+        es = spec(np.eye(op.N) - fa.apply_inv(P, fo.dense_K(op)))
+        assert es < bound, (kind, es)
+    buf, _ = build_operator("linear1d", 64, 1e-10, 1e-10, hif_rescale=True)
+    G = fa.dense_G(fa.PackedFactors(buf))
+    assert np.max(np.abs(G - np.eye(64) / 64)) < 1e-12
