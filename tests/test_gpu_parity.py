@@ -31,6 +31,7 @@ CASES = {
     "ex1_1024": ("ex1", 1024, 1e-10, 1e-9),
     "ex3_32": ("ex3", 32, 1e-5, 1e-3),
     "ex2b_1024": ("ex2b", 1024, 1e-7, 1e-6),   # Example 2, sigma^2 = 0.05 (variable amplitude)
+    "ex3_32_rescaled": ("ex3", 32, 1e-5, 1e-3, True),  # Cholesky-rescaled HIF node factors
 }
 _ops = {}
 
@@ -38,8 +39,8 @@ _ops = {}
 def get(name):
     if name not in _ops:
         fbuild.build()
-        kind, n, eb, eh = CASES[name]
-        buf, info = build_operator(kind, n, eb, eh)
+        kind, n, eb, eh, *rescale = CASES[name]
+        buf, info = build_operator(kind, n, eb, eh, hif_rescale=bool(rescale and rescale[0]))
         _ops[name] = (buf, info, fa.PackedFactors(buf), binding.Operator(buf), fo.FIO(kind, n))
     return _ops[name]
 
