@@ -428,6 +428,17 @@ def main():
     except Exception as exc:
         variants["full_solve_u_eq_KFf"] = {"error": str(exc)[:200]}
 
+    # per-stage error of every precision against the FP64 path (8 right-hand sides: the
+    # tensor-core precisions need b >= 8), in application order of the inverse apply
+    stage_err = {}
+    try:
+        u8 = binding.colmajor(torch.from_numpy(u_np[:, :8]).cuda())
+        for tag, prec in (("fp32", binding.FIO_P32), ("tf32", binding.FIO_PTF32), ("bf16", binding.FIO_PBF16),
+                          ("split_tf32", binding.FIO_PTF32X3), ("double_float", binding.FIO_PDF)):
+            stage_err[tag] = [float("%.3g" % e) for e in op.stage_errors("inv", u8, prec)]
+    except Exception as exc:
+        stage_err["error"] = str(exc)[:200]
+
     # solve latency to ||u - K-dot f|| <= 1e-10 ||u||: the plain FP64 path (PCG on K*K with G, FP64
     # factors, one right-hand side per call) against FP64-residual iterative refinement whose
     # corrections run on the tensor cores, on batches of b right-hand sides
@@ -514,7 +525,7 @@ def main():
                 "rhs_N_per_s": round(value * N, 1), "wall_ms_per_step": round(1000 * t_wall / a.steps, 4),
                 "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
                 "cpu_baseline": cpu, "stages": stage_rows, "variants": variants, "solve_latency": solves,
-                "autotune": tuned, "rel_err_vs_fp64": fp32_err,
+                "autotune": tuned, "rel_err_vs_fp64": fp32_err, "stage_errors_vs_fp64": stage_err,
                 "factors": {"P_K": tot["P_K"], "P_G": tot["P_G"], "padded_K": tot["padded_K"],
                             "padded_G": tot["padded_G"], "bytes_c64": 8 * (tot["padded_K"] + tot["padded_G"]),
                             "build_s": {k: info.get(k) for k in ("t_bf", "t_peel", "t_hif", "t_total")}}}

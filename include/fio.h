@@ -200,6 +200,17 @@ int fio_autotune(fio_op op, int b, int precision, void* stream, int* choices, in
  * fit fall back to 0).  Host-only; FIO_EINVAL for a variant that does not exist for the pair. */
 int fio_set_variant(fio_op op, int b, int precision, int variant);
 
+/* Diagnostics: the error of `precision` stage by stage.  Runs the apply `which` (0 K-dot,
+ * 1 K-dot*, 2 G-dot, 3 G-dot K-dot*) on x (complex128, device, column-major, ld >= N, b >= 1)
+ * twice side by side, in FP64 and in `precision` (FIO_P32, a tensor-core precision or FIO_PDF;
+ * x rounded to its vector type), and after every stage launch group (each butterfly stage; each
+ * HIF stage and the root) stores ||y_p - y_64|| / ||y_64|| of the intermediate vectors in
+ * errs_host[k] (k < cap), in application order; *nerr receives the number of stages.  The FP64
+ * path is the one held to 1e-12 of the oracle, so these are errors against the oracle's
+ * arithmetic.  Allocates its own work vectors and synchronises `stream`. */
+int fio_stage_errors(fio_op op, int which, const void* x, int64_t ld, int b, int precision, void* stream,
+                     double* errs_host, int cap, int* nerr);
+
 /* Operator facts: dimension, grid size n, N = n^d, device bytes held (factors + scratch). */
 int fio_query(fio_op op, int* d, int64_t* n, int64_t* N, size_t* device_bytes);
 

@@ -27,8 +27,8 @@ STATUS = {0: "FIO_OK", -1: "FIO_EINVAL", -2: "FIO_ENOMEM", -3: "FIO_EBADFACTORS"
 SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G", "fio_apply_inv",
            "fio_apply_F", "fio_apply_Finv",
            "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_apply_profiled",
-           "fio_apply_inv_noalloc", "fio_selftest_wait", "fio_autotune", "fio_set_variant", "fio_release",
-           "fio_strerror"]
+           "fio_apply_inv_noalloc", "fio_selftest_wait", "fio_autotune", "fio_set_variant", "fio_stage_errors",
+           "fio_release", "fio_strerror"]
 
 _lib = None
 
@@ -71,6 +71,8 @@ def load(path: str = LIB_PATH):
     lib.fio_selftest_wait.argtypes = [c_int, c_int, ctypes.POINTER(c_int), vp]
     lib.fio_autotune.argtypes = [vp, c_int, c_int, vp, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int)]
     lib.fio_set_variant.argtypes = [vp, c_int, c_int, c_int]
+    lib.fio_stage_errors.argtypes = [vp, c_int, vp, i64, c_int, c_int, vp, ctypes.POINTER(ctypes.c_double),
+                                     c_int, ctypes.POINTER(c_int)]
     lib.fio_release.argtypes = [vp]
     lib.fio_strerror.argtypes = [c_int]
     lib.fio_strerror.restype = ctypes.c_char_p
@@ -149,6 +151,20 @@ class Operator:
     def set_variant(self, b: int, precision: int, variant: int):
         """Pin every stage launch of (precision, bucket of b) to one kernel variant (fio_set_variant)."""
         _check(self._lib.fio_set_variant(self.h, b, precision, variant), "fio_set_variant")
+
+    def stage_errors(self, which: str, x, precision: int):
+        """Relative error of `precision` against the FP64 path after every stage of the apply
+        `which` (fio_stage_errors); x: complex128 column-major device tensor."""
+        k = {"K": 0, "Kadj": 1, "G": 2, "inv": 3}[which]
+        dt, prec, b, ld = _vec(x, self.N)
+        if dt != FIO_C128:
+            raise ValueError("fio_stage_errors takes complex128 input")
+        cap = 4096
+        out = (ctypes.c_double * cap)()
+        n = ctypes.c_int()
+        _check(self._lib.fio_stage_errors(self.h, k, ctypes.c_void_p(x.data_ptr()), ld, b, precision, _stream(),
+                                          out, cap, ctypes.byref(n)), "fio_stage_errors")
+        return [out[i] for i in range(min(n.value, cap))]
 
     def launches(self, which: str, b: int) -> int:
         k = {"K": 0, "Kadj": 1, "G": 2, "inv": 3}[which]

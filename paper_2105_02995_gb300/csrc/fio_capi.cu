@@ -1078,6 +1078,139 @@ extern "C" int fio_autotune(fio_op op, int b, int precision, void* stream, int* 
 }
 
 // ---------------------------------------------------------------------------------------------
+// fio_stage_errors: per-stage error of a precision against the FP64 path (see fio.h)
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 to_d2(dfc v) { return make_double2((double)v.rh + v.rl, (double)v.ih + v.il); }
+
+// acc[0] += sum |a - ref|^2, acc[1] += sum |ref|^2 over n values
+template <typename V>
+__global__ void k_diff_norm(const V* a, const double2* ref, long long n, double* acc) {
+  double d = 0.0, r = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 u = to_d2(a[i]), v = ref[i];
+    const double ex = u.x - v.x, ey = u.y - v.y;
+    d += ex * ex + ey * ey;
+    r += v.x * v.x + v.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+    r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&acc[0], d);
+    atomicAdd(&acc[1], r);
+  }
+}
+
+__global__ void k_to_c64(const double2* a, float2* b, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = make_float2((float)a[t].x, (float)a[t].y);
+}
+void convert_in(const double2* a, float2* b, long long n, cudaStream_t s) {
+  k_to_c64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n);
+}
+void convert_in(const double2* a, dfc* b, long long n, cudaStream_t s) {
+  k_split_df<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, (size_t)n);
+}
+
+template <typename V>
+int stage_errors_t(fio_op op, int which, const void* x, int64_t ld, int b, cudaStream_t s, double* errs, int cap,
+                   int* nerr) {
+  const size_t len = (size_t)op->max_len * b;
+  double2 *A64 = nullptr, *B64 = nullptr, *W64 = nullptr;
+  V *A = nullptr, *B = nullptr, *W = nullptr;
+  double* acc = nullptr;
+  bool ok = cudaMalloc(&A64, len * sizeof(double2)) == cudaSuccess &&
+            cudaMalloc(&B64, len * sizeof(double2)) == cudaSuccess &&
+            cudaMalloc(&W64, len * sizeof(double2)) == cudaSuccess && cudaMalloc(&A, len * sizeof(V)) == cudaSuccess &&
+            cudaMalloc(&B, len * sizeof(V)) == cudaSuccess && cudaMalloc(&W, len * sizeof(V)) == cudaSuccess &&
+            cudaMalloc(&acc, 2 * sizeof(double)) == cudaSuccess;
+  int rc = ok ? FIO_OK : FIO_ENOMEM;
+  int k = 0;
+  auto record = [&](const double2* ref, const V* val, long long n) {
+    if (rc) return;
+    double h[2] = {0.0, 0.0};
+    cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
+    k_diff_norm<V><<<1024, 256, 0, s>>>(val, ref, n, acc);
+    if (cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = FIO_ECUDA;
+      return;
+    }
+    if (k < cap) errs[k] = h[1] > 0.0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
+    ++k;
+  };
+  if (rc == FIO_OK) {
+    const long long N = op->N;
+    to_row<double2>((const double2*)x, ld, W64, N, b, s);  // both chains start from the same values
+    convert_in(W64, W, N * b, s);
+    if (which != 2) {
+      const bool adj = which != 0;
+      const double2* c64 = W64;
+      const V* c = W;
+      for (int kk = 0; kk < op->n_bf && rc == FIO_OK; ++kk) {
+        const Stage& st = op->st[adj ? op->n_bf - 1 - kk : kk];
+        double2* d64 = (kk & 1) ? B64 : A64;
+        V* d = (kk & 1) ? B : A;
+        launch_stage<double2>(st, adj, c64, b, 1, d64, b, 1, b, s);
+        launch_stage<V>(st, adj, c, b, 1, d, b, 1, b, s);
+        record(d64, d, (adj ? st.in_len : st.out_len) * (long long)b);
+        c64 = d64;
+        c = d;
+      }
+      if (which == 3 && rc == FIO_OK && op->n_bf > 0) {
+        cudaMemcpyAsync(W64, c64, (size_t)N * b * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(W, c, (size_t)N * b * sizeof(V), cudaMemcpyDeviceToDevice, s);
+      }
+    }
+    if (which >= 2) {
+      const int h0 = op->n_bf, nh = op->n_hif;
+      auto step = [&](const Stage& st, bool adj) {
+        inplace_stage<double2>(st, adj, W64, A64, b, s);
+        inplace_stage<V>(st, adj, W, A, b, s);
+        record(W64, W, N * b);
+      };
+      for (int t = 0; t < nh && rc == FIO_OK; ++t) step(op->st[h0 + t], false);
+      for (int t = 0; t < op->n_root && rc == FIO_OK; ++t) step(op->st[h0 + nh + t], false);
+      for (int t = nh - 1; t >= 0 && rc == FIO_OK; --t) step(op->st[h0 + t], true);
+    }
+    if (rc == FIO_OK && cudaGetLastError() != cudaSuccess) rc = FIO_ECUDA;
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(A64);
+  cudaFree(B64);
+  cudaFree(W64);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(W);
+  cudaFree(acc);
+  cudaGetLastError();
+  if (nerr) *nerr = k;
+  if (rc == FIO_OK && fio_tc_timeout_reset() > 0) rc = FIO_ETIMEOUT;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int fio_stage_errors(fio_op op, int which, const void* x, int64_t ld, int b, int precision, void* stream,
+                                double* errs, int cap, int* nerr) {
+  if (!op || !x || which < 0 || which > 3 || b <= 0 || ld < op->N || cap < 0 || (cap > 0 && !errs)) return FIO_EINVAL;
+  if (precision == FIO_P64 || precision < FIO_P64 || precision > FIO_PDF) return FIO_EINVAL;
+  if (precision == FIO_PDF ? !op->arena_df : !op->arena32) return FIO_EINVAL;
+  if (is_tc_precision(precision) && !op->arena_tc) return FIO_EINVAL;
+  if (which >= 2 && op->n_root == 0) return FIO_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaGetLastError() != cudaSuccess) return FIO_ECUDA;
+  if (precision == FIO_PDF) return stage_errors_t<dfc>(op, which, x, ld, b, s, errs, cap, nerr);
+  TcMode m(tc_mode_of(precision));
+  return stage_errors_t<float2>(op, which, x, ld, b, s, errs, cap, nerr);
+}
+
+// ---------------------------------------------------------------------------------------------
 // fio_apply_inv_noalloc: the direct solve with scratch in a static device array
 // ---------------------------------------------------------------------------------------------
 // For callers that must not allocate device memory during a solve (see fio.h).  The scratch is

@@ -419,3 +419,40 @@ def test_example2_pcg_with_G_vs_cg_with_Kadj_only():
     K = fo.dense_K(ofo)
     _, it_cg, _ = fo.cgne(ofo, u[:, 0], tol=1e-8, maxit=3000, K=K)
     assert it_cg > 20 * max(i for i, _, _ in infos), (it_cg, infos)
+
+
+@pytest.mark.parametrize("name", ["ex1_1024", "ex3_32", "ex2b_1024"])
+def test_stage_errors_against_fp64(name):
+    """fio_stage_errors reports one error per stage launch group; its last entry is the error of
+    the whole apply (the same kernels run).  On the well-conditioned operators every precision
+    stays within its apply bound; on Example 2 (sigma^2 = 0.05) the HIF stages amplify every
+    precision's rounding alike, so the largest stage error is bounded by the FP32 path's largest
+    times the ratio of the input roundings (TF32: the tensor core keeps 10 mantissa bits of an
+    FP32 operand, 2^-10 / 2^-24 = 2^14; BF16 rounds to 8 bits, 2^-9 / 2^-24, bound 2^16; split
+    TF32: 3 x 2^-22 per product plus the truncating accumulation, bound 2^8), and double-float
+    stays below FP32."""
+    buf, info, P, op, ofo = get(name)
+    b = 8
+    x = complex_gaussian(ofo.N, b, rhs_seed(0, 900))
+    xd = dev(x)
+    ref = op.apply_inv(xd).cpu().numpy()
+    nst = P.n_bf + 2 * P.n_hif + P.n_root
+    bounds = {binding.FIO_PDF: 1e-11, binding.FIO_P32: TOL32, binding.FIO_PTF32X3: TOL_TC[binding.FIO_PTF32X3],
+              binding.FIO_PTF32: TOL_TC[binding.FIO_PTF32], binding.FIO_PBF16: TOL_TC[binding.FIO_PBF16]}
+    ratio = {binding.FIO_PDF: 1.0, binding.FIO_P32: 1.0, binding.FIO_PTF32X3: 2.0 ** 8,
+             binding.FIO_PTF32: 2.0 ** 14, binding.FIO_PBF16: 2.0 ** 16}
+    errs32 = op.stage_errors("inv", xd, binding.FIO_P32)
+    for prec, bound in bounds.items():
+        errs = op.stage_errors("inv", xd, prec)
+        assert len(errs) == nst, (prec, len(errs), nst)
+        if name == "ex2b_1024":
+            assert max(errs) <= ratio[prec] * max(errs32) * 1.01, (prec, max(errs), max(errs32))
+        else:
+            assert max(errs) < bound, (prec, errs)
+        # the last stage's error is the whole apply's error against the FP64 apply
+        dt = torch.complex128 if prec == binding.FIO_PDF else torch.complex64
+        y = op.apply_inv(xd.to(dt), precision=prec).cpu().numpy().astype(np.complex128)
+        whole = rel(y, ref)
+        assert abs(errs[-1] - whole) <= 0.05 * whole + 1e-15, (prec, errs[-1], whole)
+    kerr = op.stage_errors("K", xd, binding.FIO_P32)
+    assert len(kerr) == P.n_bf and max(kerr) < TOL32
