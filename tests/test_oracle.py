@@ -238,3 +238,73 @@ def test_ex2_normal_matrix_hpd_and_harder():
         assert ev.min() > 0
         conds[kind] = ev.max() / ev.min()
     assert conds["ex1"] < conds["ex2a"] < conds["ex2b"], conds
+
+
+# ---- planted mistakes: each plausible error in the oracle's K must fail one of its pins ----------
+
+def _golden_mismatches(K_block):
+    bad = 0
+    for kind, n, r, c, num, den in _golden_rows():
+        got = K_block(fo.FIO(kind, n), [r], [c])[0, 0]
+        bad += abs(got - np.exp(2j * np.pi * num / den)) > 1e-12
+    return bad
+
+
+def test_planted_mistakes_fail_the_golden_phases():
+    """Transposed operand, a dropped phase term, a shifted frequency grid and a wrong sign of the
+    smooth part each change hand-worked entries of tests/golden/phase_values.txt."""
+    assert _golden_mismatches(fo.K_block) == 0
+
+    def transposed(op, rows, cols):
+        return fo.K_block(op, cols, rows)
+
+    def dropped_smooth(op, rows, cols):  # Phi = x.xi only
+        lin = fo.FIO("linear1d" if op.d == 1 else "linear2d", op.n)
+        return fo.K_block(lin, rows, cols)
+
+    def shifted_grid(op, rows, cols):   # xi = j instead of j - n/2
+        k, _ = fo.grid(op, np.asarray(cols))
+        shift = np.asarray(cols) + (op.n // 2 if op.d == 1 else (op.n // 2) * (1 + op.n))
+        return fo.K_block(op, rows, np.mod(shift, op.N))
+
+    def conj_phase(op, rows, cols):
+        return np.conj(fo.K_block(op, rows, cols))
+
+    for wrong in (transposed, dropped_smooth, shifted_grid, conj_phase):
+        assert _golden_mismatches(wrong) > 0, wrong.__name__
+
+
+def test_planted_dft_mistakes_fail_the_definition():
+    """A wrong sign of the exponent or a missing (-1)^k modulation in F^{-1} disagrees with the dense
+    definition of F (tests above pin apply_Finv against it)."""
+    n, d = 16, 1
+    rng = np.random.default_rng(14)
+    g = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    want = np.linalg.solve(fo.F_matrix(n, d), g)
+    assert fo.rel_err(fo.apply_Finv(n, d, g), want) < 1e-12
+    no_mod = np.fft.ifft(g) * n                 # (-1)^k modulation dropped
+    wrong_sign = _mod(n) * np.fft.fft(g)        # exp(-2 pi i k j / n) instead of exp(+...)
+    assert fo.rel_err(no_mod, want) > 0.1
+    assert fo.rel_err(wrong_sign, want) > 0.1
+
+
+def _mod(n):
+    return np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+
+
+def test_planted_amplitude_mistake_fails_the_golden_amplitudes():
+    """A non-periodic distance in x (plain x - x_k) changes the hand-worked Example 2 amplitudes."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "ex2_amplitude.txt")
+    sigma2 = {"ex2a": 0.1, "ex2b": 0.05}
+    bad = 0
+    with open(path) as fh:
+        for line in fh:
+            if not line.strip() or line.startswith("#"):
+                continue
+            kind, n, r, c, *q = line.split()
+            n, r, c = int(n), int(r), int(c)
+            want = sum(np.exp(-(int(v) / 64.0) / sigma2[kind]) for v in q)
+            x, eta = r / n, (c - n // 2) / n
+            plain = sum(np.exp(-((x - xk) ** 2 + (eta - ek) ** 2) / sigma2[kind]) for xk, ek in fo.EX2_CENTRES)
+            bad += abs(plain - want) > 1e-12 * want
+    assert bad > 0
