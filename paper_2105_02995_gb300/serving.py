@@ -93,6 +93,12 @@ class Server:
         self.budget = hbm_budget if hbm_budget is not None else int(0.5 * free)
         self.resident = resident
 
+    def close(self):
+        """Stop the solve-mode worker threads (they are idle between runs)."""
+        for ex in self.workers.values():
+            ex.shutdown(wait=True)
+        self.workers = {}
+
     def _batch_bytes(self, name, b):
         N = self.ops[name].N
         if self.mode == "solve":  # u, f in complex128 and the solver's work vectors
@@ -259,6 +265,7 @@ def main(argv=None):
     rate = a.load * cap / 32.5  # requests per second (mean 32.5 right-hand sides each)
     reqs = poisson_requests(ops, a.requests, rate, a.seed)
     stats = srv.run(reqs)
+    srv.close()
     out = {"mix": sorted(ops), "mode": a.mode, "precision": a.precision, "capacity_rhs_per_s": cap,
            "offered_requests_per_s": rate, **stats.summary()}
     print(json.dumps(out))
