@@ -456,3 +456,22 @@ def test_stage_errors_against_fp64(name):
         assert abs(errs[-1] - whole) <= 0.05 * whole + 1e-15, (prec, errs[-1], whole)
     kerr = op.stage_errors("K", xd, binding.FIO_P32)
     assert len(kerr) == P.n_bf and max(kerr) < TOL32
+
+
+@pytest.mark.parametrize("kind,n", [("linear1d", 256), ("linear2d", 16)])
+def test_linear_phase_degenerate_case(kind, n):
+    """Phi = x.xi: K*K = N I, so the HIF eliminates every DOF at the leaves (empty root) and
+    G-dot K-dot* = K*/N; and K = F^{-1}, so the butterfly apply and the FFT kernel (two
+    independent GPU paths) must agree to the butterfly tolerance."""
+    fbuild.build()
+    buf, info = build_operator(kind, n, 1e-10, 1e-10)
+    assert info["root"] == 0
+    op = binding.Operator(buf)
+    ofo = fo.FIO(kind, n)
+    u = complex_gaussian(ofo.N, 3, rhs_seed(0, 950))
+    f = host(op.apply_inv(dev(u)))
+    assert rel(f, fo.apply_Kadj(ofo, u) / ofo.N) < 1e-9
+    kb = host(op.apply_K(dev(u)))
+    fi = host(op.apply_Finv(dev(u)))
+    assert rel(kb, fi) < 1e-9
+    assert rel(fi, fo.apply_K(ofo, u)) < 1e-13
