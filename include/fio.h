@@ -144,7 +144,7 @@ int fio_apply_inv(fio_op op, const void* u, void* f, int64_t ld, int b, int dtyp
  *   fio_apply_F     f-hat(xi) = n^{-d} sum_x exp(-2 pi i x.xi) f(x)
  *   fio_apply_Finv  f(x)      =         sum_xi exp(+2 pi i x.xi) f-hat(xi)
  * on the operator's grids (x = k/n, xi = j - n/2 per dimension, 2D index i1 + n*i2), for n a
- * power of two and N = n^d <= 2048^2 (FIO_ENOTSUP otherwise).  Vectors as for the applies;
+ * power of two and N = n^d <= 2048^2 (FIO_ENOTSUP otherwise), b <= 65535.  Vectors as for the applies;
  * complex128 in FP64 (FIO_P64) or complex64 in FP32 (FIO_P32).  Batched shared-memory FFT
  * (one pass for 1D N <= 2048, else two: rows and columns in 2D, four-step in 1D). */
 int fio_apply_F(fio_op op, const void* f, void* fhat, int64_t ld, int b, int dtype, int precision,

@@ -225,7 +225,7 @@ int apply_dft(fio_op op, bool inverse, const void* x, void* y, long long ld, int
 
 int dft_entry(fio_op op, bool inverse, const void* x, void* y, int64_t ld, int b, int dtype, int precision,
               void* stream) {
-  if (!op || b < 0 || ld < (op ? op->N : 0)) return FIO_EINVAL;
+  if (!op || b < 0 || b > 65535 || ld < (op ? op->N : 0)) return FIO_EINVAL;  // b: grid rows
   if (!((dtype == FIO_C128 && precision == FIO_P64) || (dtype == FIO_C64 && precision == FIO_P32)))
     return FIO_EINVAL;
   if (b > 0 && (!x || !y || x == y)) return FIO_EINVAL;
