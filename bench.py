@@ -13,6 +13,16 @@ host before timing (cached on disk between runs of the same box).
 Multi-GPU: replicas only (the right-hand sides are independent): every rank applies its own
 batch with its own copy of the factors; no collective on the data path.
 
+Before timing, every stage launch's kernel variant is picked by the autotuner (fio_autotune) for
+the batches timed here (--no-autotune keeps the built-in shapes).  Beside the headline the JSON
+line carries: roofline (FLOP/s of the stage launches against the FP32 CUDA-core peak, DRAM
+traffic per apply from the committed ncu capture), e2e (host buffers through fio_apply_inv_host),
+cpu_baseline (the oracle), the tensor-core variants and the full solve f = F^{-1} G K* u,
+per-stage errors of every precision against the FP64 path, and solve latencies to residual
+1e-10 (plain FP64 PCG one right-hand side at a time against iterative refinement on batches).
+--kind / --n / --eps-bf / --eps-hif select another operator (e.g. Example 2: --kind ex2b --n
+65536 --eps-bf 1e-7 --eps-hif 1e-4).
+
 --impl reference times the oracle (oracle/factor_apply.py: the same factors multiplied out as
 sparse matrices in FP64 on the host cores) on a bounded sample of the same workload.
 """
