@@ -182,3 +182,14 @@ def test_rescaled_hif_accuracy():
     buf, _ = build_operator("linear1d", 64, 1e-10, 1e-10, hif_rescale=True)
     G = fa.dense_G(fa.PackedFactors(buf))
     assert np.max(np.abs(G - np.eye(64) / 64)) < 1e-12
+
+
+@pytest.mark.parametrize("kind,n,eb,eh", [("ex1", 256, 1e-7, 1e-6), ("ex3", 16, 1e-5, 1e-3)])
+def test_G_is_hermitian_positive_definite(kind, n, eb, eh):
+    """G-dot = R_L...R_1 A_0^{-1} R_1*...R_L* is Hermitian positive definite for any invertible node
+    factors (A_0 is HPD): the factor oracle's G of a real operator must be, so a node factor applied
+    untransposed, in the wrong order, or dropped on one side shows up here."""
+    buf, _ = build_operator(kind, n, eb, eh)
+    G = fa.dense_G(fa.PackedFactors(buf))
+    assert np.linalg.norm(G - G.conj().T) < 1e-12 * np.linalg.norm(G)
+    assert np.linalg.eigvalsh(0.5 * (G + G.conj().T)).min() > 0

@@ -85,3 +85,4 @@ def test_bad_magic():
     buf[0:8] = b"XXXXXXXX"
     with pytest.raises(ValueError):
         fa.PackedFactors(bytes(buf))
+

@@ -308,3 +308,15 @@ def test_planted_amplitude_mistake_fails_the_golden_amplitudes():
             plain = sum(np.exp(-((x - xk) ** 2 + (eta - ek) ** 2) / sigma2[kind]) for xk, ek in fo.EX2_CENTRES)
             bad += abs(plain - want) > 1e-12 * want
     assert bad > 0
+
+
+def test_cgne_matrix_free_equals_dense():
+    """The oracle's matrix-free CG (its mode for N too large for a dense K) follows the same
+    iterates as the dense mode: same iteration count, same solution to rounding."""
+    op = fo.FIO("ex1", 128)
+    rng = np.random.default_rng(15)
+    u = rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)
+    f_d, it_d, r_d = fo.cgne(op, u, tol=1e-12, K=fo.dense_K(op))
+    f_m, it_m, r_m = fo.cgne(op, u, tol=1e-12)
+    assert it_d == it_m
+    assert fo.rel_err(f_m, f_d) < 1e-11
