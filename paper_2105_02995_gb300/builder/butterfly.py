@@ -42,6 +42,11 @@ from .geometry import Tree
 from .stages import KIND_MAP, ROLE_BF, Stage
 
 
+# range of a sampled block: singular directions above RANGE_REL * eps of the largest are kept (the
+# range must be resolved well below eps for the least-squares coefficients to reach eps)
+RANGE_REL = 1e-3
+
+
 def _rank(sv: np.ndarray, eps: float) -> int:
     if sv.size == 0 or sv[0] == 0:
         return 0
@@ -62,7 +67,7 @@ def lowrank_block(ent: FIOEntries, P: np.ndarray, Q: np.ndarray, eps: float,
         c = np.sort(rng.choice(n2, sc, replace=False))
         Kc = ent.block(P, Q[c])
         Uc, svc, _ = np.linalg.svd(Kc, full_matrices=False)
-        k1 = int(np.count_nonzero(svc > 1e-3 * eps * svc[0]))
+        k1 = int(np.count_nonzero(svc > RANGE_REL * eps * svc[0]))
         Qb = Uc[:, :k1]
         # rows: the k1 rows a pivoted QR of Qb^* selects (they keep Qb[rho] well conditioned),
         # plus random rows up to the sample size
