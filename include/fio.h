@@ -44,7 +44,11 @@
  *
  * ERRORS.  Every call returns an int status: FIO_OK (0) or a negative FIO_E* code; nothing is
  * thrown and nothing aborts.  Launch errors and errors of earlier asynchronous work found at the
- * call return FIO_ECUDA.  fio_strerror gives a static message.
+ * call return FIO_ECUDA.  fio_strerror gives a static message.  The tensor-core kernels bound
+ * every wait; one that gives up sets a per-device flag and leaves its outputs incomplete.  The
+ * asynchronous applies cannot see that flag when they return: it is reported (FIO_ETIMEOUT) and
+ * cleared by the next synchronising call on the device -- fio_sync, fio_apply_inv_host,
+ * fio_solve, fio_apply_profiled, fio_autotune or fio_stage_errors.
  *
  * PACKED FACTOR BUFFER (little-endian; produced by paper_2105_02995_gb300/builder/pack.py):
  *   header, 256 bytes:
@@ -153,7 +157,8 @@ int fio_apply_Finv(fio_op op, const void* fhat, void* f, int64_t ld, int b, int 
                    void* stream);
 
 /* As fio_apply_inv, but u and f are HOST pointers (pageable or pinned): the call copies u to the
- * device, applies, copies f back and synchronises `stream` before returning. */
+ * device, applies, copies f back and synchronises `stream` before returning.  FIO_ETIMEOUT when a
+ * tensor-core bounded wait gave up (f is then incomplete). */
 int fio_apply_inv_host(fio_op op, const void* u_host, void* f_host, int64_t ld, int b, int dtype,
                        int precision, void* stream);
 
@@ -256,6 +261,11 @@ int fio_apply_inv_noalloc(fio_op op, const void* u, void* f, int64_t ld, int b, 
  * bad arguments, FIO_ECUDA / FIO_ENOMEM otherwise.  Synchronises `stream`; leaves the device
  * usable.  This is how the library's failure path is tested without a device fault or hang. */
 int fio_selftest_wait(int limit_us, int nblocks, int* gave_up, void* stream);
+
+/* Synchronise `stream` and report what the asynchronous calls before it left: FIO_ETIMEOUT when a
+ * tensor-core bounded wait on the current device gave up since the last synchronising call (the
+ * flag is then cleared), FIO_ECUDA when the stream holds a CUDA error, else FIO_OK. */
+int fio_sync(void* stream);
 
 /* Free the device copies and scratch of op (synchronises the device first).  NULL is a no-op. */
 int fio_release(fio_op op);

@@ -35,6 +35,10 @@ Functions and their pins (tests/test_oracle.py):
   normal_matrix                           pinned: diag = N exactly, Hermitian positive definite,
                                           = N I for the linear phase
   cgne                                    pinned: agrees with solve_lu; true residual
+  spectral_norm_est                       the power iteration of the paper's e_a / e_s estimates
+                                          (section 6); pinned: ||K||_2 = sqrt(N) for the linear
+                                          phase, diagonal, rank-one and a non-normal 2 x 2 closed
+                                          form (a planted adjoint without conjugation fails)
   F_matrix, apply_F, apply_Finv           the DFT f-hat = F f of section 1 (definition written out
                                           densely; numpy.fft as the library DFT for large n)
                                           pinned: dense definition vs numpy.fft, F^{-1} = the

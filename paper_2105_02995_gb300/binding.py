@@ -28,7 +28,7 @@ SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G",
            "fio_apply_F", "fio_apply_Finv",
            "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_apply_profiled",
            "fio_apply_inv_noalloc", "fio_selftest_wait", "fio_autotune", "fio_set_variant", "fio_stage_errors",
-           "fio_release", "fio_strerror"]
+           "fio_sync", "fio_release", "fio_strerror"]
 
 _lib = None
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
     lib.fio_set_variant.argtypes = [vp, c_int, c_int, c_int]
     lib.fio_stage_errors.argtypes = [vp, c_int, vp, i64, c_int, c_int, vp, ctypes.POINTER(ctypes.c_double),
                                      c_int, ctypes.POINTER(c_int)]
+    lib.fio_sync.argtypes = [vp]
     lib.fio_release.argtypes = [vp]
     lib.fio_strerror.argtypes = [c_int]
     lib.fio_strerror.restype = ctypes.c_char_p
@@ -277,6 +278,11 @@ class Operator:
         if rc not in (0, -4):
             _check(rc, "fio_solve")
         return f, [(infos[j].iters, infos[j].relres, infos[j].status) for j in range(b)]
+
+    def sync(self):
+        """Synchronise the current stream; raises FioError(FIO_ETIMEOUT) when a tensor-core
+        bounded wait gave up in an earlier asynchronous apply (fio_sync)."""
+        _check(self._lib.fio_sync(_stream()), "fio_sync")
 
     def release(self):
         if getattr(self, "h", None):

@@ -889,7 +889,20 @@ extern "C" int fio_apply_inv_host(fio_op op, const void* u_host, void* f_host, i
   if (rc) return rc;
   if (cudaMemcpy2DAsync(f_host, (size_t)ld * es, F, w, w, (size_t)b, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return FIO_ECUDA;
-  return cudaStreamSynchronize(s) == cudaSuccess ? FIO_OK : FIO_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FIO_ECUDA;
+  // a tensor-core bounded wait that gave up left part of f unwritten: report it here, at the
+  // call that produced the result, not at some later synchronising call
+  const int to = fio_tc_timeout_reset();
+  return to < 0 ? FIO_ECUDA : (to > 0 ? FIO_ETIMEOUT : FIO_OK);
+}
+
+extern "C" int fio_sync(void* stream) {
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return FIO_ECUDA;
+  }
+  const int to = fio_tc_timeout_reset();
+  return to < 0 ? FIO_ECUDA : (to > 0 ? FIO_ETIMEOUT : FIO_OK);
 }
 
 extern "C" int fio_launch_count(fio_op op, int which, int b, int* launches) {
@@ -1271,12 +1284,16 @@ extern "C" int fio_apply_inv_noalloc(fio_op op, const void* u, void* f, int64_t 
   cudaStream_t s = (cudaStream_t)stream;
   // Nothing here needs clearing: every stage writes all of its outputs before a later stage
   // reads them, so contents left by an earlier call are never read.
-  if (precision == FIO_P64)
+  if (precision == FIO_P64) {
     inv_with_buffers<double2>(op, (const double2*)u, (double2*)f, ld, b, (double2*)p,
                               (double2*)(p + per), (double2*)(p + 2 * per), s);
-  else
+  } else {
+    // the stage arithmetic of the complex64 path (FP32 CUDA cores or a tensor-core mode), as in
+    // fio_apply_inv
+    TcMode m(tc_mode_of(precision));
     inv_with_buffers<float2>(op, (const float2*)u, (float2*)f, ld, b, (float2*)p,
                              (float2*)(p + per), (float2*)(p + 2 * per), s);
+  }
   return finish(s);
 }
 

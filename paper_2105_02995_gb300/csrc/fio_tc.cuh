@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
   constexpr uint32_t TA = X3 ? 32768u : 16384u;  // bytes of the A tile(s)
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_drain;  // after a timeout: every MMA issued has finished
   extern __shared__ __align__(16) uint8_t smem_dyn[];
   // layout: A tile (16 KB, 1024-byte aligned for the swizzle atoms; split mode: A_hi then A_lo),
   // B tile (N x 128 B; split mode: B_hi then B_lo), x staging (KC rows x nmax/2 complex), gather list
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
   if (warp == 0) tmem_alloc(&s_tmem, ncol_tmem);
   if (tid == 0) {
     mbar_init(&s_bar, 1);
+    mbar_init(&s_drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // the block's gather list, once per CTA: the per-chunk copies then never wait on it
@@ -337,7 +339,18 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
     fence_after();
   }
   cp_wait_all();
-  if (!ok && tid == 0) atomicExch(&g_tc_timeout, 1);
+  if (!ok) {
+    // a wait gave up with MMAs possibly still in flight: thread 0 (which issued all of them)
+    // commits once more, and the CTA waits (bounded) for that commit before the tiles and the
+    // tensor memory are released
+    if (tid == 0) {
+      atomicExch(&g_tc_timeout, 1);
+      mma_commit(&s_drain);
+    }
+    __syncthreads();
+    mbar_wait(&s_drain, 0);
+    fence_after();
+  }
 
   // epilogue: warp w holds accumulator rows 32w .. 32w+31 (TMEM lanes)
   const int row = r0 + warp * 32 + lane;

@@ -193,3 +193,37 @@ def test_G_is_hermitian_positive_definite(kind, n, eb, eh):
     G = fa.dense_G(fa.PackedFactors(buf))
     assert np.linalg.norm(G - G.conj().T) < 1e-12 * np.linalg.norm(G)
     assert np.linalg.eigvalsh(0.5 * (G + G.conj().T)).min() > 0
+
+
+def test_example3_64_errors_against_the_paper_table():
+    """Example 3 at 64^2 (N = 4096) with the paper's eps = 1e-3 and eps_BF = 1e-4, against the
+    paper's Table for Example 3 (e_a 9.62e-5, e_s 2.13e-3 at 64^2), both estimated as the paper
+    does (section 6: randomized power iteration, here oracle.spectral_norm_est, pinned against
+    closed forms) on matrix-free products with the oracle's dense K:
+      * e_a = ||K - K-dot|| / ||K|| within 2x the paper's value (measured 1.16e-4);
+      * e_s = ||I - G-dot K-dot* K|| within 4x the paper's value: the 2D ID threshold read as
+        relative to ||A|| as well (reading R18) eliminates fewer DOFs at 16 x 16 cells than the
+        paper's code, and e_s lands at 3x the paper's (measured 6.6e-3; dense SVD 6.6e-3);
+        and at most 10 eps.
+    G-dot is Hermitian (test_G_is_hermitian_positive_definite), so E* = I - K* K-dot G-dot."""
+    n, eb, eh = 64, 1e-4, 1e-3
+    buf, info = built("ex3", n, eb, eh)
+    P = fa.PackedFactors(buf)
+    op = fo.FIO("ex3", n)
+    K = fo.dense_K(op)
+    N = op.N
+
+    def Dop(x, adj):
+        return (fa.apply_Kdot_adj(P, x) - K.conj().T @ x) if adj else (fa.apply_Kdot(P, x) - K @ x)
+
+    ea = fo.spectral_norm_est(Dop, N, iters=30) / fo.spectral_norm_est(
+        lambda x, adj: K.conj().T @ x if adj else K @ x, N, iters=30)
+
+    def Eop(x, adj):
+        if adj:
+            return x - K.conj().T @ fa.apply_Kdot(P, fa.apply_G(P, x))
+        return x - fa.apply_inv(P, K @ x)
+
+    es = fo.spectral_norm_est(Eop, N, iters=40)
+    assert ea < 2 * 9.62e-5, ea
+    assert es < 4 * 2.13e-3 and es < 10 * eh, es

@@ -5,49 +5,12 @@ product is worked out by hand, so these tests depend neither on the product's pa
 oracle's own arithmetic.
 """
 
-import struct
-
 import numpy as np
 import pytest
 
 from oracle import factor_apply as fa
 
-
-def _checksum(data: bytes) -> int:
-    words = struct.unpack("<%dQ" % (len(data) // 8), data)
-    return sum(w * (2 * k + 1) for k, w in enumerate(words)) % (1 << 64)
-
-
-def hand_pack(N, bf, hif, root, d=1):
-    """bf/hif/root: lists of (kind, M[nblk,R,C], in[nblk,C], out[nblk,R], in_len, out_len)."""
-    stages = bf + hif + root
-    tab = 256
-    data = tab + 64 * len(stages)
-    data = (data + 255) // 256 * 256
-    blobs = []
-    entries = []
-    cur = data
-    for kind, M, ii, oo, il, ol in stages:
-        offs = []
-        for arr in (np.asarray(M, "<c16"), np.asarray(ii, "<i4"), np.asarray(oo, "<i4")):
-            b = arr.tobytes()
-            b += b"\0" * ((-len(b)) % 256)
-            offs.append(cur)
-            blobs.append(b)
-            cur += len(b)
-        nblk, R, C = np.asarray(M).shape
-        entries.append(struct.pack("<IIIIqqQQQQ", kind, nblk, R, C, il, ol, *offs, 0))
-    body = b"".join(blobs)
-    head = bytearray(data)
-    head[0:8] = b"FIOPACK1"
-    struct.pack_into("<II", head, 8, 1, d)
-    struct.pack_into("<qq", head, 16, N, N)
-    struct.pack_into("<IIII", head, 32, len(bf), len(hif), len(root), 0)
-    struct.pack_into("<dd", head, 48, 1e-6, 1e-6)
-    struct.pack_into("<QQQQ", head, 64, tab, data, data + len(body), _checksum(body))
-    for s, e in enumerate(entries):
-        head[tab + 64 * s: tab + 64 * (s + 1)] = e
-    return bytes(head) + body
+from handpack import hand_pack
 
 
 def _tiny():
@@ -86,3 +49,24 @@ def test_bad_magic():
     with pytest.raises(ValueError):
         fa.PackedFactors(bytes(buf))
 
+
+
+def test_plumbing_operator_stays_in_small_integers():
+    """The exact-integer operator of tests/handpack.py: on inputs with integer parts in {-1, 0, 1}
+    every intermediate vector of K-dot, K-dot*, G-dot and G-dot K-dot* has integer parts of
+    modulus <= 256, which every precision of the library represents exactly (bfloat16 has an
+    8-bit significand); the GPU plumbing tests rely on this."""
+    from handpack import plumbing_operator
+    P = fa.PackedFactors(plumbing_operator())
+    rng = np.random.default_rng(0)
+    x = rng.integers(-1, 2, (P.N, 6)) + 1j * rng.integers(-1, 2, (P.N, 6))
+    # stage by stage, in every order the applies use
+    seqs = {"K": [(m, False) for m in P.bf], "Kadj": [(m, True) for m in reversed(P.bf)],
+            "G": [(m, False) for m in P.hif] + [(m, False) for m in P.root] + [(m, True) for m in reversed(P.hif)]}
+    seqs["inv"] = seqs["Kadj"] + seqs["G"]
+    for name, seq in seqs.items():
+        v = x.astype(complex)
+        for m, adj in seq:
+            v = (m.conj().T @ v) if adj else (m @ v)
+            for part in (v.real, v.imag):
+                assert np.all(part == np.round(part)) and np.abs(part).max() <= 256, name

@@ -2,10 +2,14 @@
 
 Two references, both from oracle/:
   * factor_apply: the same packed factors multiplied out as sparse matrices in FP64.  The FP64
-    GPU path must agree to 1e-12 (relative, Frobenius); the FP32 path to TOL32 below.
+    GPU path must agree to 1e-12 relative; the FP32 path to TOL32 below.  "Relative" is the
+    larger of the Frobenius ratio ||a - b|| / ||b|| and the element-wise max|a - b| / max|b|, so
+    a few wrong rows cannot hide in the norm of a large array.
   * fio_oracle: the dense K and its LU solve (the plain definition); the direct solve must be
     within 10 eps of it at these sizes, iterative solves must reach the residual they report.
 Sizes span several blocks per stage and ragged right-hand-side tiles (b = 1, 3, 5, 16, 37).
+Example 3 at n = 64 (N = 4096) is the smallest 2D operator with HIF edge stages (section 4.2,
+the edge skeletonization R-bar_l, here at level 2).
 
 TOL32: every stage rounds its outputs to FP32 (unit roundoff 2^-24 ~ 6e-8) after sums of up to
 C_max ~ 300 terms, over up to ~20 stages in a row: 20 * sqrt(300) * 6e-8 ~ 2e-5 relative.
@@ -30,6 +34,7 @@ CASES = {
     "ex1_256": ("ex1", 256, 1e-7, 1e-6),     # the 1D N = 256, eps = 1e-6 workload
     "ex1_1024": ("ex1", 1024, 1e-10, 1e-9),
     "ex3_32": ("ex3", 32, 1e-5, 1e-3),
+    "ex3_64": ("ex3", 64, 1e-5, 1e-3),       # first size with 2D edge stages
     "ex2b_1024": ("ex2b", 1024, 1e-7, 1e-6),   # Example 2, sigma^2 = 0.05 (variable amplitude)
     "ex3_32_rescaled": ("ex3", 32, 1e-5, 1e-3, True),  # Cholesky-rescaled HIF node factors
 }
@@ -53,8 +58,15 @@ def host(t):
     return t.cpu().numpy().astype(np.complex128)
 
 
+def frob(a, b):
+    """||a - b||_F / ||b||_F (the norm of the paper's error measures)."""
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
 def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    """max(||a - b||_F / ||b||_F, max|a - b| / max|b|)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return max(float(np.linalg.norm(a - b) / np.linalg.norm(b)), float(np.abs(a - b).max() / np.abs(b).max()))
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -82,13 +94,15 @@ def test_apply_fp32_vs_factor_oracle(name, b):
         assert rel(host(y), ref(P, x.astype(np.complex64).astype(np.complex128))) < TOL32, what
 
 
-@pytest.mark.parametrize("name", ["ex1_256", "ex3_32"])
+@pytest.mark.parametrize("name", ["ex1_256", "ex3_32", "ex3_64"])
 def test_direct_solve_vs_dense_lu(name):
-    """f = G-dot K-dot* u on the GPU against K^{-1} u by dense LU: within 10 eps."""
+    """f = G-dot K-dot* u on the GPU against K^{-1} u by dense LU: within 10 eps (an error of
+    the approximation, bounded in norm by the paper's e_s = ||I - G-dot K-dot* K||_2, so
+    measured in the Frobenius norm)."""
     buf, info, P, op, ofo = get(name)
     u = complex_gaussian(ofo.N, 4, rhs_seed(0))
     f = host(op.apply_inv(dev(u)))
-    assert rel(f, fo.solve_lu(ofo, u)) < 10 * CASES[name][3]
+    assert frob(f, fo.solve_lu(ofo, u)) < 10 * CASES[name][3]
 
 
 def test_leading_dimension_and_host_entry():
@@ -173,7 +187,7 @@ def _tc_apply(op, fn, xd, b, prec):
     return rc, y
 
 
-@pytest.mark.parametrize("name", ["ex1_256", "ex3_32"])
+@pytest.mark.parametrize("name", ["ex1_256", "ex3_32", "ex3_64"])
 @pytest.mark.parametrize("prec", TC_PRECS)
 @pytest.mark.parametrize("b", [8, 32, 40, 72])
 def test_apply_tensor_core_vs_factor_oracle(name, prec, b):
@@ -190,7 +204,7 @@ def test_apply_tensor_core_vs_factor_oracle(name, prec, b):
         assert err < TOL_TC[prec], (what, err)
 
 
-@pytest.mark.parametrize("name", ["ex1_256", "ex3_32"])
+@pytest.mark.parametrize("name", ["ex1_256", "ex3_32", "ex3_64"])
 def test_split_tf32_removes_tf32_rounding(name):
     """The split products are two orders of magnitude closer to the oracle than plain TF32 (a
     kernel that dropped the tail products would land at the TF32 error), and of the FP32 path's
@@ -452,7 +466,7 @@ def test_stage_errors_against_fp64(name):
         # the last stage's error is the whole apply's error against the FP64 apply
         dt = torch.complex128 if prec == binding.FIO_PDF else torch.complex64
         y = op.apply_inv(xd.to(dt), precision=prec).cpu().numpy().astype(np.complex128)
-        whole = rel(y, ref)
+        whole = frob(y, ref)
         assert abs(errs[-1] - whole) <= 0.05 * whole + 1e-15, (prec, errs[-1], whole)
     kerr = op.stage_errors("K", xd, binding.FIO_P32)
     assert len(kerr) == P.n_bf and max(kerr) < TOL32

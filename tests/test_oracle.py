@@ -320,3 +320,37 @@ def test_cgne_matrix_free_equals_dense():
     f_m, it_m, r_m = fo.cgne(op, u, tol=1e-12)
     assert it_d == it_m
     assert fo.rel_err(f_m, f_d) < 1e-11
+
+
+# ---- spectral_norm_est: the power iteration behind the e_a / e_s estimates (section 6) --------
+
+@pytest.mark.parametrize("kind,n", [("linear1d", 64), ("linear2d", 8)])
+def test_spectral_norm_linear_phase_is_sqrt_N(kind, n):
+    """Phi = x.xi: K*K = N I (K is N times a unitary DFT up to signs), so ||K||_2 = sqrt(N).  A
+    power iteration that returned the eigenvalue of K*K instead of its square root would give N."""
+    op = fo.FIO(kind, n)
+    est = fo.spectral_norm_est(lambda x, adj: fo.apply_Kadj(op, x) if adj else fo.apply_K(op, x), op.N, iters=5)
+    assert abs(est - np.sqrt(op.N)) < 1e-12 * np.sqrt(op.N)
+
+
+def test_spectral_norm_closed_forms():
+    """Closed forms: a diagonal matrix (the largest modulus, with a spectral gap so that the
+    iteration converges), a rank-one matrix u v* (||u|| ||v||, reached after one step), and a
+    non-normal matrix whose adjoint must be applied as the conjugate transpose (a planted
+    adjoint without the conjugation changes the answer)."""
+    d = np.array([0.5, -3.0 + 4.0j, 1.0, 2.0j, 0.1])  # |d| max = 5, next 2
+    diag = fo.spectral_norm_est(lambda x, adj: (np.conj(d) if adj else d) * x, 5, iters=60)
+    assert abs(diag - 5.0) < 1e-12
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(7) + 1j * rng.standard_normal(7)
+    v = rng.standard_normal(7) + 1j * rng.standard_normal(7)
+    A = np.outer(u, v.conj())
+    r1 = fo.spectral_norm_est(lambda x, adj: (A.conj().T if adj else A) @ x, 7, iters=3)
+    assert abs(r1 - np.linalg.norm(u) * np.linalg.norm(v)) < 1e-12 * r1
+    # [[1, 1j], [0, 1]]: ||A||_2 = (1 + sqrt 5) / 2 (golden ratio; A*A = [[1, 1j], [-1j, 2]])
+    B = np.array([[1.0, 1j], [0.0, 1.0]])
+    gold = (1 + np.sqrt(5)) / 2
+    est = fo.spectral_norm_est(lambda x, adj: (B.conj().T if adj else B) @ x, 2, iters=60)
+    assert abs(est - gold) < 1e-12
+    wrong = fo.spectral_norm_est(lambda x, adj: (B.T if adj else B) @ x, 2, iters=60)
+    assert abs(wrong - gold) > 1e-3
