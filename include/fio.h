@@ -112,6 +112,10 @@ typedef struct {
   int restart;   /* GMRES restart length (FIO_GMRES, and the inner GMRES of FIO_IR)             */
   int outer;     /* fio_precision of the residuals u - K-dot f on complex128 vectors: FIO_P64   */
                  /* (0, FP64 arithmetic) or FIO_PDF (double-float arithmetic)                   */
+  fio_op residual_op; /* operator whose K-dot gives the true residuals (NULL: the solved         */
+                 /* operator itself); FIO_IR and FIO_DIRECT only.  A butterfly of the same FIO  */
+                 /* (same d and n) built with a smaller tolerance: refinement then solves       */
+                 /* K-dot_tight f = u, with the loose operator's G-dot K-dot* as the correction */
 } fio_solve_opts;
 
 typedef struct {
@@ -170,11 +174,15 @@ int fio_apply_inv_host(fio_op op, const void* u_host, void* f_host, int64_t ld, 
  *               opts->outer precision (FP64 or double-float), correction G-dot K-dot* r in
  *               opts->inner precision, FP64 update f += d.
  * Every method computes its true residuals u - K-dot f in opts->outer precision (PCG and GMRES
- * run their Krylov products in FP64 whatever opts->outer is).  An all-zero initial guess is
+ * run their Krylov products in FP64 whatever opts->outer is).  With opts->residual_op (FIO_IR,
+ * FIO_DIRECT) those residuals, and hence tol and info->relres, refer to that operator's K-dot:
+ * the approximate inverse of `op` (section 5) corrects towards the solution of the tighter
+ * butterfly, whose distance to the exact K is its own e_a.  An all-zero initial guess is
  * detected and its residual taken as u without an apply.
  * f holds the initial guess on entry (zero it for none) and the solution on return.  dtype must
  * be FIO_C128 (FP64 solution).  info_host (may be NULL) receives one record per right-hand side;
- * the call synchronises `stream`.  Returns FIO_OK, FIO_ENOCONV, or an error code. */
+ * the call synchronises `stream`.  Returns FIO_OK, FIO_ENOCONV, or an error code (FIO_EINVAL
+ * also for a residual_op of another grid, with another method, or lacking opts->outer's copy). */
 int fio_solve(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
               const fio_solve_opts* opts, fio_solve_info* info_host, void* stream);
 

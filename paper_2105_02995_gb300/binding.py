@@ -41,7 +41,8 @@ class FioError(RuntimeError):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("inner", ctypes.c_int), ("tol", ctypes.c_double),
-                ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("outer", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("outer", ctypes.c_int),
+                ("residual_op", ctypes.c_void_p)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -262,16 +263,19 @@ class Operator:
         return f
 
     def solve(self, u, f=None, method: int = FIO_GMRES, inner: int = FIO_P64, tol: float = 1e-10,
-              maxit: int = 100, restart: int = 20, outer: int = FIO_P64):
+              maxit: int = 100, restart: int = 20, outer: int = FIO_P64, residual_op=None):
         """Iterative solve of K-dot f = u (complex128 tensors); returns (f, list of (iters, relres, status)).
-        outer = FIO_PDF computes the true residuals in double-float arithmetic."""
+        outer = FIO_PDF computes the true residuals in double-float arithmetic; residual_op (an
+        Operator of the same grid with a tighter butterfly; FIO_IR and FIO_DIRECT) takes them
+        with that operator's K-dot instead."""
         import torch
         if f is None:
             f = torch.zeros_like(u)
         dt, prec, b, ld = _vec(u, self.N)
         if dt != FIO_C128:
             raise ValueError("fio_solve takes complex128 vectors")
-        opts = SolveOpts(method, inner, tol, maxit, restart, outer)
+        opts = SolveOpts(method, inner, tol, maxit, restart, outer,
+                         residual_op.h.value if residual_op is not None else None)
         infos = (SolveInfo * max(b, 1))()
         rc = self._lib.fio_solve(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(f.data_ptr()),
                                  ld, b, dt, ctypes.byref(opts), infos, _stream())

@@ -2,6 +2,7 @@
 // K-dot (paper section 2), K-dot* , G-dot (section 4) and G-dot K-dot* (section 5), and the
 // operator bookkeeping.  The iterative solvers live in fio_solve.cu.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -18,6 +19,7 @@
 #include "fio_internal.h"
 #include "fio_kernels.cuh"
 #include "fio_tc.cuh"
+#include "fio_tma.cuh"
 
 using namespace fio;
 
@@ -57,6 +59,85 @@ bool is_permutation(const int32_t* idx, size_t n, int64_t len) {
     ++cnt;
   }
   return cnt == len;
+}
+
+// cuTensorMapEncodeTiled from the driver (looked up once; no link-time dependency on libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2D tensor map over a stage's factor copy for the TMA kernel: rows = nblk * rows_per_blk, each of
+// 2 * ld elements (FP32 or BF16), boxes of 32 rows x 128 bytes (four make one 128-row operand
+// tile), 128-byte swizzle (the K-major operand layout of tcgen05.mma).  False when the copy's base or row stride is not 16-byte
+// aligned (the stage then keeps the other kernels).
+bool encode_tmap(CUtensorMap* map, const void* base, bool bf16, long long rows, int ld) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn || !base || rows <= 0 || ld <= 0) return false;
+  const int esz = bf16 ? 2 : 4;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * ld), (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(2 * ld) * esz};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)tma::kBoxRows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  if (((uintptr_t)base & 15) || (strides[0] & 15) || rows > 0x7fffffffLL) return false;
+  return fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base),
+            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// work units of the TMA kernel for one stage: per direction and per unit size G in {1, 2, 4}
+// row tiles, every block's 128-row tiles in groups of at most G, sorted by work (tiles x valid
+// columns) with the largest first, so that the persistent CTAs' round-robin walk ends evenly
+int build_units(fio_op op, const std::vector<int2>& meta, const std::vector<size_t>& mdims) {
+  static const int kG[3] = {1, 2, 4};
+  std::vector<int4> all;
+  std::vector<size_t> off;
+  for (size_t si = 0; si < op->st.size(); ++si) {
+    const Stage& st = op->st[si];
+    for (int dir = 0; dir < 2; ++dir)
+      for (int g = 0; g < 3; ++g) {
+        std::vector<std::pair<long long, int4>> u;
+        for (uint32_t b = 0; b < st.nblk; ++b) {
+          const int2 d = meta[mdims[si] + b];
+          const int rows = dir ? d.y : d.x, cols = dir ? d.x : d.y;
+          const int nt = (rows + kTcRows - 1) / kTcRows;
+          for (int t0 = 0; t0 < nt; t0 += kG[g]) {
+            const int k = std::min(kG[g], nt - t0);
+            u.push_back(std::make_pair((long long)k * cols, make_int4((int)b, t0, k, 0)));
+          }
+        }
+        std::stable_sort(u.begin(), u.end(), [](const std::pair<long long, int4>& x, const std::pair<long long, int4>& y) {
+          return x.first > y.first;
+        });
+        off.push_back(all.size());
+        for (auto& e : u) all.push_back(e.second);
+      }
+  }
+  off.push_back(all.size());
+  if (all.empty()) return FIO_OK;
+  if (cudaMalloc(&op->units, all.size() * sizeof(int4)) != cudaSuccess) {
+    cudaGetLastError();
+    return FIO_ENOMEM;
+  }
+  op->units_bytes = all.size() * sizeof(int4);
+  if (cudaMemcpy(op->units, all.data(), op->units_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return FIO_ECUDA;
+  size_t k = 0;
+  for (auto& st : op->st)
+    for (int dir = 0; dir < 2; ++dir)
+      for (int g = 0; g < 3; ++g, ++k) {
+        st.units[dir][g] = (const int4*)op->units + off[k];
+        st.nunits[dir][g] = (int)(off[k + 1] - off[k]);
+      }
+  return FIO_OK;
 }
 
 }  // namespace
@@ -284,6 +365,19 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
       k_to_bf16<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(st.M32, bf, (int)st.nblk, (int)st.R, (int)st.C, st.ldbf);
       k_to_bf16<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(t32, bft, (int)st.nblk, (int)st.C, (int)st.R, st.ldbft);
     }
+    // the TMA kernel's tensor maps (forward / adjoint x FP32 / BF16) and work units
+    for (auto& st : op->st) {
+      const long long nb = st.nblk;
+      st.tma_ok[0][0] = encode_tmap(&st.tmap[0][0], st.M32, false, nb * st.R, (int)st.C);
+      st.tma_ok[1][0] = encode_tmap(&st.tmap[1][0], st.M32t, false, nb * st.C, (int)st.R);
+      st.tma_ok[0][1] = encode_tmap(&st.tmap[0][1], st.Mbf, true, nb * st.R, st.ldbf);
+      st.tma_ok[1][1] = encode_tmap(&st.tmap[1][1], st.Mbft, true, nb * st.C, st.ldbft);
+    }
+    const int urc = build_units(op, meta, mdims);
+    if (urc != FIO_OK) {
+      fio_release(op);
+      return urc;
+    }
   }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
     fio_release(op);
@@ -300,6 +394,7 @@ extern "C" int fio_release(fio_op op) {
   if (op->arena32) cudaFree(op->arena32);
   if (op->arena_df) cudaFree(op->arena_df);
   if (op->meta) cudaFree(op->meta);
+  if (op->units) cudaFree(op->units);
   if (op->arena_tc) cudaFree(op->arena_tc);
   if (op->scratch) cudaFree(op->scratch);
   fio_solver_free(op);
@@ -315,7 +410,7 @@ extern "C" int fio_query(fio_op op, int* d, int64_t* n, int64_t* N, size_t* devi
   if (N) *N = op->N;
   if (device_bytes)
     *device_bytes = op->arena_bytes + op->arena32_bytes + op->arena_tc_bytes + op->arena_df_bytes + op->meta_bytes +
-                    op->scratch_bytes + op->solver_bytes;
+                    op->units_bytes + op->scratch_bytes + op->solver_bytes;
   return FIO_OK;
 }
 
@@ -498,6 +593,7 @@ bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
 // (k_stage_mm_vt): 9 <16,2,8> with 128 threads, 10 <16,2,4> with 256 threads.  Shapes 2..7, 9, 10
 // need the pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the
 // plain tiled kernel.
+constexpr int kTmaVariant = 30;  // the TMA-fed persistent tensor-core kernel (k_stage_tma)
 inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : (b <= 32 ? 3 : 4))); }
 // candidates per bucket, the built-in choice first
 constexpr int kNCand = 6;
@@ -590,6 +686,77 @@ bool launch_tc_var(const TcArgs& a, int ncta, cudaStream_t s, int var) {
   }
 }
 
+// multiprocessor count of the current device (cached per device)
+int num_sms() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = 1;
+  }
+  cache[dev] = n;
+  return n;
+}
+
+// the TMA-fed persistent kernel (variant 30); false when it does not apply to this launch:
+// x must be the row-major work layout with 16-byte aligned rows (b even), and the stage's tensor
+// map must exist
+bool launch_tma(const Stage& st, bool adj, const float2* x, long long xrs, long long xcs, float2* y, long long yrs,
+                long long ycs, int b, cudaStream_t s) {
+  const bool bf = g_tc_mode == kTcBF16;
+  const int dir = adj ? 1 : 0;
+  if (!st.tma_ok[dir][bf ? 1 : 0] || xcs != 1 || (xrs & 1) || (b & 1) || ((uintptr_t)x & 15) || b < 8) return false;
+  TmaArgs a;
+  a.rowidx = adj ? st.in : st.out;
+  a.colidx = adj ? st.out : st.in;
+  a.lrow = adj ? (int)st.C : (int)st.R;
+  a.lcol = adj ? (int)st.R : (int)st.C;
+  a.rows_per_blk = adj ? (int)st.C : (int)st.R;
+  a.dims = st.dims;
+  a.b = b;
+  a.nmax = 2 * ((std::min(b, kTcMaxRhs) + 7) & ~7);
+  // units of 4, 2 or 1 row tiles: G x nmax accumulator columns fit one of the two buffers
+  const int g = a.nmax <= (int)tma::kBufCols / 4 ? 2 : (a.nmax <= (int)tma::kBufCols / 2 ? 1 : 0);
+  a.units = st.units[dir][g];
+  a.nunits = st.nunits[dir][g];
+  a.nrhs_tiles = (b + kTcMaxRhs - 1) / kTcMaxRhs;
+  a.x = x;
+  a.xrs = xrs;
+  a.y = y;
+  a.yrs = yrs;
+  a.ycs = ycs;
+  if (!a.units) return false;
+  const long long total = (long long)a.nunits * a.nrhs_tiles;
+  if (total == 0) return true;
+  const int grid = (int)std::min<long long>(total, num_sms());
+  const int need = tma::smem_bytes(g_tc_mode, a.nmax);
+  const CUtensorMap& map = st.tmap[dir][bf ? 1 : 0];
+  switch (g_tc_mode * 2 + dir) {
+#define FIO_TMA_CASE(MODE, ADJ)                                                                   \
+  case 2 * MODE + ADJ:                                                                            \
+    if (!smem_opt_in((const void*)k_stage_tma<ADJ, MODE>, need)) return false;                   \
+    k_stage_tma<ADJ, MODE><<<grid, tma::kThreads, need, s>>>(a, map);                             \
+    return true;
+    FIO_TMA_CASE(kTcTF32, 0)
+    FIO_TMA_CASE(kTcTF32, 1)
+    FIO_TMA_CASE(kTcBF16, 0)
+    FIO_TMA_CASE(kTcBF16, 1)
+    FIO_TMA_CASE(kTcX3, 0)
+    FIO_TMA_CASE(kTcX3, 1)
+#undef FIO_TMA_CASE
+    default: return false;
+  }
+}
+
 // false when variant `var` does not apply (the caller then uses variant 0)
 bool launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long long xcs, float2* y,
                long long yrs, long long ycs, int b, cudaStream_t s, int var) {
@@ -621,6 +788,7 @@ bool launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long l
   a.nmax = 2 * ((std::min(b, kTcMaxRhs) + 7) & ~7);
   a.stage_x = (xcs == 1 && xrs % 2 == 0 && b % 2 == 0 && ((uintptr_t)x & 15) == 0) ? 1 : 0;
   a.ncmax = adj ? (int)st.R : (int)st.C;  // gather list length per block (forward: in, adjoint: out)
+  if (var == kTmaVariant) return launch_tma(st, adj, x, xrs, xcs, y, yrs, ycs, b, s);
   if (ncta == 0) return true;
   switch (g_tc_mode * 2 + (adj ? 1 : 0)) {
     case 2 * kTcTF32: return launch_tc_var<false, kTcTF32>(a, ncta, s, var);
@@ -977,7 +1145,7 @@ float time_launch(F&& launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   return best;
 }
 
-constexpr int kTcCand[4] = {0, 20, 21, 22};
+constexpr int kTcCand[5] = {0, 20, 21, 22, kTmaVariant};
 
 // tune every stage launch of one vector type at b right-hand sides; choices[] gets the variant
 // per (stage, direction) in stage order, forward before adjoint
@@ -1011,7 +1179,7 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
       if (st.nblk > 0) {
         const StageArgs<V> a = stage_args<V>(st, adj, X, b, 1, Y, b, 1, b);
         float tbest = -1.f;
-        const int ncand = tc ? 4 : kNCand;
+        const int ncand = tc ? 5 : kNCand;
         for (int k = 0; k < ncand; ++k) {
           const int var = tc ? kTcCand[k] : kCand[bucket][k];
           if (var <= 0 && !tc) break;
@@ -1055,7 +1223,7 @@ extern "C" int fio_set_variant(fio_op op, int b, int precision, int variant) {
   const bool tc = mode != 0 && b >= 8;
   int ti;
   if (tc) {
-    if (variant != 0 && (variant < 20 || variant > 22)) return FIO_EINVAL;
+    if (variant != 0 && (variant < 20 || variant > 22) && variant != kTmaVariant) return FIO_EINVAL;
     ti = 2 + mode;
   } else {
     ti = precision == FIO_P64 ? 0 : (precision == FIO_PDF ? 2 : 1);

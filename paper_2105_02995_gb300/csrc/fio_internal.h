@@ -1,6 +1,7 @@
 // fio_internal.h -- operator object shared by the translation units of libfio (not installed).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -43,6 +44,15 @@ struct Stage {
   // split TF32][direction: forward, adjoint][right-hand-side bucket]; 0 = the built-in choice
   // (see fio_capi.cu)
   int8_t var[6][2][5] = {};
+  // TMA tensor maps of the tensor-core A operands per [direction: forward (M32 / Mbf), adjoint
+  // (M32t / Mbft)][element: FP32, BF16]; tma_ok marks the maps that encoded (16-byte aligned
+  // rows and base)
+  CUtensorMap tmap[2][2];
+  bool tma_ok[2][2] = {};
+  // work units of the TMA kernel per [direction][at most 1, 2, 4 row tiles per unit]: (block,
+  // first 128-row tile, tiles, 0), largest first
+  const int4* units[2][3] = {};
+  int nunits[2][3] = {};
 };
 
 }  // namespace fio
@@ -66,6 +76,8 @@ struct fio_op_s {
   size_t arena_df_bytes = 0;
   void* meta = nullptr;           // per-block dims and tile lists of every stage
   size_t meta_bytes = 0;
+  void* units = nullptr;          // work-unit lists of the TMA kernel (every stage)
+  size_t units_bytes = 0;
   void* solver = nullptr;         // solver work arrays (fio_solve.cu)
   size_t solver_bytes = 0;
 };

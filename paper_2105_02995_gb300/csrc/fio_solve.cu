@@ -169,6 +169,7 @@ int get_work(fio_op op, int b, int restart, Work* w) {
 
 struct Ctx {
   fio_op op;
+  fio_op rop;           // operator of the true residuals (op itself, or a tighter butterfly)
   long long N;
   int b;
   cudaStream_t s;
@@ -229,7 +230,7 @@ int residual(Ctx& c, const double2* u, long long ld, const double2* f, double2* 
                ? FIO_OK
                : FIO_ECUDA;
   }
-  int rc = fio_apply_internal(c.op, 0, f, s, ld, c.b, c.outer, c.s);
+  int rc = fio_apply_internal(c.rop, 0, f, s, ld, c.b, c.outer, c.s);
   if (rc) return rc;
   std::vector<double2> one(c.b, make_double2(1, 0)), mone(c.b, make_double2(-1, 0));
   // s holds K f with ld = ld; bring it to ld N: s = u - s
@@ -257,6 +258,12 @@ extern "C" int fio_solve(fio_op op, const void* uv, void* fv, int64_t ld, int b,
   if (is_tc_precision(opts->inner) && !op->arena_tc) return FIO_EINVAL;
   if (opts->outer != FIO_P64 && opts->outer != FIO_PDF) return FIO_EINVAL;
   if (opts->outer == FIO_PDF && !op->arena_df) return FIO_EINVAL;
+  fio_op rop = opts->residual_op ? opts->residual_op : op;
+  if (rop != op) {
+    if (opts->method != FIO_IR && opts->method != FIO_DIRECT) return FIO_EINVAL;
+    if (rop->d != op->d || rop->n != op->n || rop->N != op->N) return FIO_EINVAL;
+    if (opts->outer == FIO_PDF ? !rop->arena_df : !rop->arena) return FIO_EINVAL;
+  }
   if (op->n_root == 0) return FIO_ENOTSUP;
   if (b == 0) return FIO_OK;
   const int maxit = opts->maxit > 0 ? opts->maxit : 100;
@@ -265,7 +272,7 @@ extern "C" int fio_solve(fio_op op, const void* uv, void* fv, int64_t ld, int b,
   Work w;
   int rc = get_work(op, b, restart, &w);
   if (rc) return rc;
-  Ctx c{op, op->N, b, s, w.sc};
+  Ctx c{op, rop, op->N, b, s, w.sc};
   c.outer = opts->outer;
   const double2* u = (const double2*)uv;
   double2* f = (double2*)fv;

@@ -94,16 +94,16 @@ def test_host_buffer_entry_is_exact(b):
         assert np.array_equal(f.astype(np.complex128), fa.apply_inv(P, x)), (dt, b)
 
 
+@pytest.mark.parametrize("b", [40, 72])
 @pytest.mark.parametrize("prec,dtype,variants", [
     (binding.FIO_P64, torch.complex128, list(range(1, 8))),
     (binding.FIO_PDF, torch.complex128, list(range(1, 8))),
     (binding.FIO_P32, torch.complex64, list(range(1, 8)) + [9, 10]),
-    (binding.FIO_PTF32, torch.complex64, [20, 21, 22]),
-    (binding.FIO_PBF16, torch.complex64, [20, 21, 22]),
-    (binding.FIO_PTF32X3, torch.complex64, [20, 21, 22])])
-def test_every_kernel_variant_is_exact(prec, dtype, variants):
+    (binding.FIO_PTF32, torch.complex64, [20, 21, 22, 30]),
+    (binding.FIO_PBF16, torch.complex64, [20, 21, 22, 30]),
+    (binding.FIO_PTF32X3, torch.complex64, [20, 21, 22, 30])])
+def test_every_kernel_variant_is_exact(prec, dtype, variants, b):
     op, P = get()
-    b = 40
     x = int_inputs(P.N, b, 4000)
     xd = binding.colmajor(torch.from_numpy(x).to("cuda", dtype))
     want = {w: ref(P, x) for w, ref in REFS.items()}
