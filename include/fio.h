@@ -270,6 +270,14 @@ int fio_apply_inv_noalloc(fio_op op, const void* u, void* f, int64_t ld, int b, 
  * usable.  This is how the library's failure path is tested without a device fault or hang. */
 int fio_selftest_wait(int limit_us, int nblocks, int* gave_up, void* stream);
 
+/* Measurement utility (no paper counterpart): the device's FP32 FMA throughput, the roofline of
+ * the CUDA-core stage kernels.  Times a kernel of independent FMA chains (iters steps of 8
+ * chains per thread, 8 CTAs of 256 threads per multiprocessor) with CUDA events on `stream`,
+ * best of three launches after one warm-up; *tflops (host) receives 2 x FMAs / time, *ms (may be
+ * NULL) that time, *sms (may be NULL) the multiprocessor count.  Synchronises `stream`.
+ * FIO_EINVAL for iters outside 1..2^24 or a NULL tflops. */
+int fio_probe_fp32(int iters, double* tflops, float* ms, int* sms, void* stream);
+
 /* Synchronise `stream` and report what the asynchronous calls before it left: FIO_ETIMEOUT when a
  * tensor-core bounded wait on the current device gave up since the last synchronising call (the
  * flag is then cleared), FIO_ECUDA when the stream holds a CUDA error, else FIO_OK. */

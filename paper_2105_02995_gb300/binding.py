@@ -28,7 +28,7 @@ SYMBOLS = ["fio_upload_factors", "fio_apply_K", "fio_apply_Kadj", "fio_apply_G",
            "fio_apply_F", "fio_apply_Finv",
            "fio_apply_inv_host", "fio_solve", "fio_query", "fio_launch_count", "fio_apply_profiled",
            "fio_apply_inv_noalloc", "fio_selftest_wait", "fio_autotune", "fio_set_variant", "fio_stage_errors",
-           "fio_sync", "fio_release", "fio_strerror"]
+           "fio_sync", "fio_probe_fp32", "fio_release", "fio_strerror"]
 
 _lib = None
 
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
     lib.fio_stage_errors.argtypes = [vp, c_int, vp, i64, c_int, c_int, vp, ctypes.POINTER(ctypes.c_double),
                                      c_int, ctypes.POINTER(c_int)]
     lib.fio_sync.argtypes = [vp]
+    lib.fio_probe_fp32.argtypes = [c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float),
+                                   ctypes.POINTER(c_int), vp]
     lib.fio_release.argtypes = [vp]
     lib.fio_strerror.argtypes = [c_int]
     lib.fio_strerror.restype = ctypes.c_char_p
@@ -88,6 +90,15 @@ def load(path: str = LIB_PATH):
 def _check(rc: int, what: str):
     if rc != 0:
         raise FioError(rc, what)
+
+
+def probe_fp32(iters: int = 1 << 16):
+    """Measured FP32 FMA throughput of the current device (fio_probe_fp32): (TFLOP/s, ms, SMs)."""
+    lib = load()
+    tf, ms, sms = ctypes.c_double(), ctypes.c_float(), ctypes.c_int()
+    _check(lib.fio_probe_fp32(iters, ctypes.byref(tf), ctypes.byref(ms), ctypes.byref(sms), _stream()),
+           "fio_probe_fp32")
+    return tf.value, ms.value, sms.value
 
 
 def colmajor(t):

@@ -295,20 +295,20 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
     return FIO_ECUDA;
   }
   if (mask & FIO_MASK_P32) {
-    if (cudaMalloc(&op->arena32, m_elems * sizeof(float2) + 256) != cudaSuccess) {
+    if (cudaMalloc(&op->arena32, (m_elems + nst) * sizeof(float2) + 256) != cudaSuccess) {
       cudaGetLastError();
       fio_release(op);
       return FIO_ENOMEM;
     }
-    op->arena32_bytes = m_elems * sizeof(float2) + 256;
+    op->arena32_bytes = (m_elems + nst) * sizeof(float2) + 256;
   }
   if (mask & FIO_MASK_DF) {
-    if (cudaMalloc(&op->arena_df, m_elems * sizeof(dfc) + 256) != cudaSuccess) {
+    if (cudaMalloc(&op->arena_df, (m_elems + nst) * sizeof(dfc) + 256) != cudaSuccess) {
       cudaGetLastError();
       fio_release(op);
       return FIO_ENOMEM;
     }
-    op->arena_df_bytes = m_elems * sizeof(dfc) + 256;
+    op->arena_df_bytes = (m_elems + nst) * sizeof(dfc) + 256;
   }
   size_t off32 = 0;
   for (auto& st : op->st) {
@@ -328,7 +328,7 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
       st.Mdf = dst;
       if (ne) k_split_df<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(st.M64, dst, ne);
     }
-    off32 += ne;
+    off32 += ne + (ne & 1);  // every stage's complex64 blocks start 16-byte aligned
   }
   if ((mask & FIO_MASK_TC) && op->arena32) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -801,12 +801,19 @@ bool launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long l
 }
 
 template <typename V>
-bool use_tc(const Stage& st, int b) {
+bool use_tc(const Stage& st, int b, bool adj) {
   return false;
 }
+// the tensor-core kernels copy operand rows in 16-byte pieces: the stage's A operand (forward: the
+// complex64 or bf16 blocks, adjoint: their transposed copies) must have 16-byte aligned rows and
+// base (the builder pads widths to even; a hand-packed odd width keeps the FP32 CUDA cores)
 template <>
-bool use_tc<float2>(const Stage& st, int b) {
-  return g_tc_mode != 0 && b >= 8 && st.M32t != nullptr;
+bool use_tc<float2>(const Stage& st, int b, bool adj) {
+  if (g_tc_mode == 0 || b < 8 || st.M32t == nullptr) return false;
+  if (g_tc_mode == kTcBF16) return true;  // bf16 rows padded to a multiple of 4 complex, 256-byte bases
+  const void* A = adj ? (const void*)st.M32t : (const void*)st.M32;
+  const uint32_t ld = adj ? st.R : st.C;
+  return (ld & 1) == 0 && ((uintptr_t)A & 15) == 0;
 }
 
 template <typename V> constexpr int type_index();
@@ -842,7 +849,7 @@ template <typename V>
 void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long long xcs, V* y,
                   long long yrs, long long ycs, int b, cudaStream_t s) {
   if (st.nblk == 0) return;
-  if (use_tc<V>(st, b)) {
+  if (use_tc<V>(st, b, adj)) {
     const int tv = st.var[2 + g_tc_mode][adj ? 1 : 0][rhs_bucket(b)];
     if (!launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s, tv))
       launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s, 0);
@@ -1173,7 +1180,7 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
     const bool root = si >= op->n_bf + op->n_hif;
     for (int dir = 0; dir < (root ? 1 : 2) && rc == FIO_OK; ++dir) {
       const bool adj = dir == 1;
-      const bool tc = use_tc<V>(st, b);
+      const bool tc = use_tc<V>(st, b, adj);
       const int ti = tc ? 2 + g_tc_mode : type_index<V>();
       int best = 0;
       if (st.nblk > 0) {
@@ -1463,6 +1470,61 @@ extern "C" int fio_apply_inv_noalloc(fio_op op, const void* u, void* f, int64_t 
                              (float2*)(p + per), (float2*)(p + 2 * per), s);
   }
   return finish(s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// fio_probe_fp32: measured FP32 FMA throughput of the device (the roofline of the CUDA-core path)
+// ---------------------------------------------------------------------------------------------
+namespace {
+// every thread runs 8 independent FMA chains of `iters` steps (enough independent work to fill
+// the FMA pipes: 8 chains x 8 warps per scheduler); the sum is stored so nothing is removed
+__global__ void __launch_bounds__(256) k_fma_probe(float* out, int iters, float a, float b) {
+  float x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (float)(threadIdx.x + k) * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], a, b);
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += x[k];
+  if (t == 12345.678f) out[blockIdx.x] = t;  // (practically) never taken, but not removable
+}
+}  // namespace
+
+extern "C" int fio_probe_fp32(int iters, double* tflops, float* ms, int* sms, void* stream) {
+  if (iters <= 0 || iters > (1 << 24) || !tflops) return FIO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nsm = num_sms();
+  const int blocks = nsm * 8;  // 8 CTAs of 256 threads per SM: 64 warps, full occupancy
+  float* d = nullptr;
+  if (cudaMalloc(&d, sizeof(float) * blocks) != cudaSuccess) {
+    cudaGetLastError();
+    return FIO_ENOMEM;
+  }
+  cudaEvent_t e0, e1;
+  int rc = FIO_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = FIO_ECUDA;
+  float best = -1.f;
+  for (int rep = 0; rc == FIO_OK && rep < 4; ++rep) {  // first launch warms up; best of the rest
+    cudaEventRecord(e0, s);
+    k_fma_probe<<<blocks, 256, 0, s>>>(d, iters, 0.999f, 1e-3f);
+    cudaEventRecord(e1, s);
+    float t = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = FIO_ECUDA;
+    if (rep > 0 && (best < 0.f || t < best)) best = t;
+  }
+  if (rc == FIO_OK) {
+    *tflops = 2.0 * 8.0 * iters * 256.0 * blocks / (best * 1e-3) / 1e12;
+    if (ms) *ms = best;
+    if (sms) *sms = nsm;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  cudaGetLastError();
+  return rc;
 }
 
 // ---------------------------------------------------------------------------------------------
