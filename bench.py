@@ -300,7 +300,10 @@ def main():
     tuned = {}
     if not a.no_autotune:
         t0 = time.perf_counter()
-        for tb, tp, tag in ((b, binding.FIO_P32, f"fp32_b{b}"), (b, binding.FIO_PDF, f"df_b{b}"),
+        for tb, tp, tag in ((b, binding.FIO_P32, f"fp32_b{b}"), (b, binding.FIO_PTF32, f"tf32_b{b}"),
+                            (b, binding.FIO_PBF16, f"bf16_b{b}"), (b, binding.FIO_PTF32X3, f"split_tf32_b{b}"),
+                            (b, binding.FIO_PDF, f"df_b{b}"), (16, binding.FIO_PTF32X3, "split_tf32_b16"),
+                            (128, binding.FIO_PTF32X3, "split_tf32_b128"),
                             (1, binding.FIO_P64, "fp64_b1"), (1, binding.FIO_P32, "fp32_b1"),
                             (1, binding.FIO_PDF, "df_b1"), (16, binding.FIO_PDF, "df_b16"),
                             (128, binding.FIO_PDF, "df_b128")):

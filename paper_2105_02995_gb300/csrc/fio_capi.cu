@@ -244,6 +244,8 @@ extern "C" int fio_upload_factors(const void* packed, size_t nbytes, unsigned ma
       for (uint32_t c = 0; c < st.C; ++c)
         if (ii[(size_t)b * st.C + c] >= 0) cb = (int)c + 1;
       meta.push_back(make_int2(rb, cb));
+      st.maxcols[0] = std::max(st.maxcols[0], cb);
+      st.maxcols[1] = std::max(st.maxcols[1], rb);
     }
     mfwd[si] = meta.size();
     for (uint32_t b = 0; b < st.nblk; ++b)
@@ -593,7 +595,8 @@ bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
 // (k_stage_mm_vt): 9 <16,2,8> with 128 threads, 10 <16,2,4> with 256 threads.  Shapes 2..7, 9, 10
 // need the pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the
 // plain tiled kernel.
-constexpr int kTmaVariant = 30;  // the TMA-fed persistent tensor-core kernel (k_stage_tma)
+constexpr int kTmaVariant = 30;       // the TMA-fed persistent tensor-core kernel (k_stage_tma)
+constexpr int kTmaSplitVariant = 31;  // the same, in-place stages split over the K dimension
 inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : (b <= 32 ? 3 : 4))); }
 // candidates per bucket, the built-in choice first
 constexpr int kNCand = 6;
@@ -711,7 +714,7 @@ int num_sms() {
 // x must be the row-major work layout with 16-byte aligned rows (b even), and the stage's tensor
 // map must exist
 bool launch_tma(const Stage& st, bool adj, const float2* x, long long xrs, long long xcs, float2* y, long long yrs,
-                long long ycs, int b, cudaStream_t s) {
+                long long ycs, int b, cudaStream_t s, int ksplit = 1, float2* part = nullptr, int gsel = -1) {
   const bool bf = g_tc_mode == kTcBF16;
   const int dir = adj ? 1 : 0;
   if (!st.tma_ok[dir][bf ? 1 : 0] || xcs != 1 || (xrs & 1) || (b & 1) || ((uintptr_t)x & 15) || b < 8) return false;
@@ -725,20 +728,34 @@ bool launch_tma(const Stage& st, bool adj, const float2* x, long long xrs, long 
   a.b = b;
   a.nmax = 2 * ((std::min(b, kTcMaxRhs) + 7) & ~7);
   // units of 4, 2 or 1 row tiles: G x nmax accumulator columns fit one of the two buffers
-  const int g = a.nmax <= (int)tma::kBufCols / 4 ? 2 : (a.nmax <= (int)tma::kBufCols / 2 ? 1 : 0);
+  a.nrhs_tiles = (b + kTcMaxRhs - 1) / kTcMaxRhs;
+  // units of up to 4, 2 or 1 row tiles (G x nmax accumulator columns fit one of the two tensor
+  // memory buffers): the largest G that still gives every SM about eight units, so that the
+  // persistent CTAs' walk ends evenly, else single tiles
+  const int gmax = a.nmax <= (int)tma::kBufCols / 4 ? 2 : (a.nmax <= (int)tma::kBufCols / 2 ? 1 : 0);
+  int g = gmax;
+  while (g > 0 && (long long)st.nunits[dir][g] * ksplit * a.nrhs_tiles < 8LL * num_sms()) --g;
+  if (gsel >= 0) g = std::min(g, gsel);
+  a.ksplit = ksplit;
+  a.part = part;
+  a.prow = (long long)st.nblk * a.rows_per_blk;
   a.units = st.units[dir][g];
   a.nunits = st.nunits[dir][g];
-  a.nrhs_tiles = (b + kTcMaxRhs - 1) / kTcMaxRhs;
   a.x = x;
   a.xrs = xrs;
   a.y = y;
   a.yrs = yrs;
   a.ycs = ycs;
   if (!a.units) return false;
-  const long long total = (long long)a.nunits * a.nrhs_tiles;
+  const long long total = (long long)a.nunits * a.ksplit * a.nrhs_tiles;
   if (total == 0) return true;
   const int grid = (int)std::min<long long>(total, num_sms());
-  const int need = tma::smem_bytes(g_tc_mode, a.nmax);
+  // as many 16 KB A slots as the 227 KB of shared memory hold (at least the split mode's tail
+  // ring of three)
+  constexpr int kSmemMax = 227 * 1024 - 1024;  // minus the kernel's static barriers
+  a.sa = std::min(tma::kMaxSA, (kSmemMax - tma::smem_fixed(g_tc_mode, a.nmax)) / 16384);
+  if (a.sa < tma::kSL) return false;
+  const int need = tma::smem_bytes(g_tc_mode, a.nmax, a.sa);
   const CUtensorMap& map = st.tmap[dir][bf ? 1 : 0];
   switch (g_tc_mode * 2 + dir) {
 #define FIO_TMA_CASE(MODE, ADJ)                                                                   \
@@ -788,7 +805,7 @@ bool launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long l
   a.nmax = 2 * ((std::min(b, kTcMaxRhs) + 7) & ~7);
   a.stage_x = (xcs == 1 && xrs % 2 == 0 && b % 2 == 0 && ((uintptr_t)x & 15) == 0) ? 1 : 0;
   a.ncmax = adj ? (int)st.R : (int)st.C;  // gather list length per block (forward: in, adjoint: out)
-  if (var == kTmaVariant) return launch_tma(st, adj, x, xrs, xcs, y, yrs, ycs, b, s);
+  if (var == kTmaVariant || var == kTmaSplitVariant) return launch_tma(st, adj, x, xrs, xcs, y, yrs, ycs, b, s);
   if (ncta == 0) return true;
   switch (g_tc_mode * 2 + (adj ? 1 : 0)) {
     case 2 * kTcTF32: return launch_tc_var<false, kTcTF32>(a, ncta, s, var);
@@ -861,10 +878,45 @@ void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long lon
   else launch_stage_dir<V, false>(a, s, var);
 }
 
-// one INPLACE stage on the row-major work vector W (scratch S has the same shape)
+// In-place stage split over K (variant 31 on the tensor cores): slices of every block's chunks as
+// separate work units of the TMA kernel (enough of them to fill the GPU: the root and the top HIF
+// levels have few, large blocks), partial sums into P, then k_partial_reduce adds the slices in a
+// fixed order straight into W (the stage's copy-back).  False when it does not apply.
 template <typename V>
-void inplace_stage(const Stage& st, bool adj, V* W, V* S, int b, cudaStream_t s) {
+bool inplace_split(const Stage&, bool, V*, V*, long long, int, cudaStream_t) {
+  return false;
+}
+template <>
+bool inplace_split<float2>(const Stage& st, bool adj, float2* W, float2* P, long long pcap, int b, cudaStream_t s) {
+  if (!P || !use_tc<float2>(st, b, adj)) return false;
+  if (st.var[2 + g_tc_mode][adj ? 1 : 0][rhs_bucket(b)] != kTmaSplitVariant) return false;
+  const int dir = adj ? 1 : 0;
+  const long long prow = (long long)st.nblk * (adj ? st.C : st.R);
+  const int units = st.nunits[dir][0];
+  if (prow <= 0 || units <= 0 || prow > pcap) return false;
+  const int kc = g_tc_mode == kTcBF16 ? 32 : 16;
+  const int nch = (st.maxcols[dir] + kc - 1) / kc;
+  // slices: about two units per SM, at least 4 chunks per slice, all slices fit in P
+  int ks = (2 * num_sms() + units - 1) / units;
+  ks = std::min<long long>(ks, std::max(1, nch / 4));
+  ks = (int)std::min<long long>(ks, pcap / prow);
+  ks = std::max(1, std::min(ks, 64));
+  if (!launch_tma(st, adj, W, b, 1, nullptr, 0, 0, b, s, ks, P, 0)) return false;
+  const long long tot = prow * b;
+  k_partial_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, ks, prow, b, st.out, W);
+  return true;
+}
+
+// one INPLACE stage on the row-major work vector W (scratch S has the same shape; P, when not
+// null, is free scratch of pcap rows for the split variant)
+template <typename V>
+void inplace_stage(const Stage& st, bool adj, V* W, V* S, int b, cudaStream_t s, V* P = nullptr,
+                   long long pcap = 0) {
   if (st.nblk == 0) return;
+  if (inplace_split<V>(st, adj, W, P, pcap, b, s)) {
+    mark(s);
+    return;
+  }
   launch_stage<V>(st, adj, W, b, 1, S, b, 1, b, s);
   const long long nidx = (long long)st.nblk * st.R;
   const long long tot = nidx * b;
@@ -912,13 +964,15 @@ void bf_chain(fio_op op, bool adj, const V* x, long long xrs, long long xcs, V* 
   }
 }
 
-// G-dot on the row-major work vector W in place; S scratch
+// G-dot on the row-major work vector W in place; S scratch; P (max_len rows) free scratch for the
+// split in-place stages
 template <typename V>
-void g_sweep(fio_op op, V* W, V* S, int b, cudaStream_t s) {
+void g_sweep(fio_op op, V* W, V* S, int b, cudaStream_t s, V* P = nullptr) {
   const int h0 = op->n_bf, nh = op->n_hif;
-  for (int t = 0; t < nh; ++t) inplace_stage<V>(op->st[h0 + t], false, W, S, b, s);
-  for (int t = 0; t < op->n_root; ++t) inplace_stage<V>(op->st[h0 + nh + t], false, W, S, b, s);
-  for (int t = nh - 1; t >= 0; --t) inplace_stage<V>(op->st[h0 + t], true, W, S, b, s);
+  const long long pc = op->max_len;
+  for (int t = 0; t < nh; ++t) inplace_stage<V>(op->st[h0 + t], false, W, S, b, s, P, pc);
+  for (int t = 0; t < op->n_root; ++t) inplace_stage<V>(op->st[h0 + nh + t], false, W, S, b, s, P, pc);
+  for (int t = nh - 1; t >= 0; --t) inplace_stage<V>(op->st[h0 + t], true, W, S, b, s, P, pc);
 }
 
 int check_args(fio_op op, const void* x, const void* y, int64_t ld, int b, int dtype, int prec) {
@@ -955,12 +1009,12 @@ void apply_core(fio_op op, Which w, const V* x, V* y, int64_t ld, int b, V* A, V
     case W_KADJ: bf_chain<V>(op, true, x, 1, ld, y, 1, ld, b, A, B, s); break;
     case W_G:
       to_row<V>(x, ld, W, op->N, b, s);
-      g_sweep<V>(op, W, A, b, s);
+      g_sweep<V>(op, W, A, b, s, B);
       to_col<V>(W, y, ld, op->N, b, s);
       break;
     case W_INV:
       bf_chain<V>(op, true, x, 1, ld, W, b, 1, b, A, B, s);
-      g_sweep<V>(op, W, A, b, s);
+      g_sweep<V>(op, W, A, b, s, B);
       to_col<V>(W, y, ld, op->N, b, s);
       break;
   }
@@ -1152,7 +1206,7 @@ float time_launch(F&& launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   return best;
 }
 
-constexpr int kTcCand[5] = {0, 20, 21, 22, kTmaVariant};
+constexpr int kTcCand[6] = {0, 20, 21, 22, kTmaVariant, kTmaSplitVariant};
 
 // tune every stage launch of one vector type at b right-hand sides; choices[] gets the variant
 // per (stage, direction) in stage order, forward before adjoint
@@ -1186,12 +1240,22 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
       if (st.nblk > 0) {
         const StageArgs<V> a = stage_args<V>(st, adj, X, b, 1, Y, b, 1, b);
         float tbest = -1.f;
-        const int ncand = tc ? 5 : kNCand;
+        const int ncand = tc ? 6 : kNCand;
         for (int k = 0; k < ncand; ++k) {
           const int var = tc ? kTcCand[k] : kCand[bucket][k];
           if (var <= 0 && !tc) break;
           float t;
-          if (tc) {
+          if (tc && st.kind == 1) {
+            // in-place stages: the whole stage (compute and copy-back, or split compute and
+            // reduction), so that the split variant is weighed with its reduction
+            t = time_launch(
+                [&] {
+                  st.var[ti][dir][bucket] = (int8_t)var;
+                  inplace_stage<V>(st, adj, X, Y, b, s, (V*)bufs[2], op->max_len);
+                  return true;
+                },
+                s, e0, e1);
+          } else if (tc) {
             t = time_launch([&] { return launch_tc(st, adj, (const float2*)X, b, 1, (float2*)Y, b, 1, b, s, var); },
                             s, e0, e1);
           } else if (adj) {
@@ -1230,7 +1294,8 @@ extern "C" int fio_set_variant(fio_op op, int b, int precision, int variant) {
   const bool tc = mode != 0 && b >= 8;
   int ti;
   if (tc) {
-    if (variant != 0 && (variant < 20 || variant > 22) && variant != kTmaVariant) return FIO_EINVAL;
+    if (variant != 0 && (variant < 20 || variant > 22) && variant != kTmaVariant && variant != kTmaSplitVariant)
+      return FIO_EINVAL;
     ti = 2 + mode;
   } else {
     ti = precision == FIO_P64 ? 0 : (precision == FIO_PDF ? 2 : 1);
@@ -1359,7 +1424,7 @@ int stage_errors_t(fio_op op, int which, const void* x, int64_t ld, int b, cudaS
       const int h0 = op->n_bf, nh = op->n_hif;
       auto step = [&](const Stage& st, bool adj) {
         inplace_stage<double2>(st, adj, W64, A64, b, s);
-        inplace_stage<V>(st, adj, W, A, b, s);
+        inplace_stage<V>(st, adj, W, A, b, s, B, op->max_len);
         record(W64, W, N * b);
       };
       for (int t = 0; t < nh && rc == FIO_OK; ++t) step(op->st[h0 + t], false);
@@ -1436,7 +1501,7 @@ template <typename V>
 void inv_with_buffers(fio_op op, const V* u, V* f, int64_t ld, int b, V* A, V* B, V* W,
                       cudaStream_t s) {
   bf_chain<V>(op, true, u, 1, ld, W, b, 1, b, A, B, s);
-  g_sweep<V>(op, W, A, b, s);
+  g_sweep<V>(op, W, A, b, s, B);
   to_col<V>(W, f, ld, op->N, b, s);
 }
 }  // namespace

@@ -31,6 +31,7 @@ struct Stage {
   const int2* tiles_fwd = nullptr;  // device, (block, tile) pairs
   const int2* tiles_adj = nullptr;
   int ntiles_fwd = 0, ntiles_adj = 0;
+  int maxcols[2] = {0, 0};  // longest valid gather list of a block: forward (cols), adjoint (rows)
   // tensor-core copies (FIO_MASK_TC): block-transposed complex64 (C x R per block), bf16 in both
   // orientations with row strides padded to a multiple of 4; 128-row tile lists
   const float2* M32t = nullptr;

@@ -11,15 +11,19 @@
 //     layout of the MMA) as up to four boxes of 32 rows, stopping at the block's last valid row
 //     (the swizzle depends on the shared-memory address only, so four 32-row boxes land exactly
 //     as one 128-row box would; rows past the block are never read from HBM and their
-//     accumulator rows are never stored), into a ring of SA stages, with an L2 evict-first
-//     policy so that the factor stream does not push the stage vectors out of L2;
+//     accumulator rows are never stored), into a ring of SA slots sized at launch to what shared
+//     memory holds (up to 11 x 16 KB: under load an HBM round trip takes microseconds, and the
+//     ring has to keep ~130 KB per SM in flight to stream at the copy rate), with an L2
+//     evict-first policy so that the factor stream does not push the stage vectors out of L2;
 //   * the CTA is persistent (one per SM) and walks a list of work units (block, first 128-row
 //     tile, up to G tiles) sorted by size; all tiles of a unit share the chunk's B tile, so the x
 //     gather and the B expansion are done once per chunk for up to G row tiles;
 //   * warp roles: warp 0 issues the TMA loads; warp 1 issues the MMAs (one elected lane);
-//     warps 2-5 gather the chunk's x rows (16-byte cp.async, two chunks ahead), expand them into
-//     the B tile and, in split-TF32 mode, split the landed A tiles into head and tail; warps 6-9
-//     read the accumulators out of tensor memory and scatter the rows;
+//     warps 2-5 gather the chunk's x rows (16-byte cp.async, two chunks ahead, their gather
+//     indices loaded one chunk earlier still), expand them into the B tile and, in split-TF32
+//     mode, split the landed A tiles into head (in place) and tail (a ring of its own, so every A
+//     slot is a TMA target); warps 6-9 read the accumulators out of tensor memory and scatter the
+//     rows;
 //   * accumulators are double-buffered in tensor memory (2 x 256 columns: all of an SM's tensor
 //     memory, so one CTA per SM), so the epilogue of a unit overlaps the MMAs of the next.
 // Every wait is bounded by %globaltimer (kWaitNs); a role whose wait gives up stops, records the
@@ -51,6 +55,11 @@ struct TmaArgs {
   long long yrs, ycs;
   int b;
   int nmax;           // accumulator columns of a full right-hand-side tile (2 x RHS padded to 8)
+  int ksplit;         // every block's chunks split into ksplit slices, one work unit each (>= 1)
+  float2* part;       // null: rows go to y; else slice ks of row r of block blk goes to
+                      // part[(ks * prow + blk * rows_per_blk + r) * b + j] (summed by k_partial_reduce)
+  long long prow;     // rows of one slice of `part` (nblk * rows_per_blk)
+  int sa;             // A ring slots (1 .. kMaxSA), set by the launcher from the shared memory
 };
 
 namespace tma {
@@ -61,20 +70,23 @@ constexpr uint32_t kBufCols = kTmemCols / 2;
 constexpr int kBoxRows = 32;         // rows per TMA box (four boxes fill one 128-row tile)
 constexpr uint32_t kATile = 16384;   // one 128 x 128-byte A tile
 constexpr int kSX = 3;               // x staging slots (gathered two chunks ahead)
+constexpr int kMaxSA = 11;           // A ring slots at most
+constexpr int kSL = 3;               // split mode: slots of the tail tiles
+constexpr int kMaxPf = 8;            // gather copies per thread and chunk at most (KC x b / 2 / 128)
 
 template <int MODE> struct Cfg {
   static constexpr bool BF16 = MODE == kTcBF16, X3 = MODE == kTcX3;
-  static constexpr int SA = X3 ? 4 : 6;                     // A ring stages
   static constexpr int SB = X3 ? 2 : 3;                     // B ring stages
-  static constexpr uint32_t ASTAGE = X3 ? 2 * kATile : kATile;  // split mode: head tile + tail tile
   static constexpr int KC = BF16 ? 32 : 16;                 // complex columns per 128-byte chunk
 };
 
-// dynamic shared memory of the kernel for accumulator width nmax (1024 bytes of alignment slack)
-__host__ __device__ constexpr int smem_bytes(int mode, int nmax) {
-  return 1024 + (mode == kTcX3 ? 4 * 2 * 16384 : 6 * 16384) +
-         (mode == kTcX3 ? 2 * 2 : 3) * nmax * 128 + kSX * (mode == kTcBF16 ? 32 : 16) * (nmax / 2) * 8;
+// dynamic shared memory besides the A ring, for accumulator width nmax: alignment slack, tail
+// ring (split mode), B ring, x staging
+__host__ __device__ constexpr int smem_fixed(int mode, int nmax) {
+  return 1024 + (mode == kTcX3 ? kSL * 16384 : 0) + (mode == kTcX3 ? 2 * 2 : 3) * nmax * 128 +
+         kSX * (mode == kTcBF16 ? 32 : 16) * (nmax / 2) * 8;
 }
+__host__ __device__ constexpr int smem_bytes(int mode, int nmax, int sa) { return smem_fixed(mode, nmax) + sa * 16384; }
 
 __device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::su32(bar)), "r"(bytes) : "memory");
@@ -109,14 +121,17 @@ template <int N>
 __device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
-// work unit u of the CTA's sequence: unit list entry and right-hand-side tile
+// work unit u of the CTA's sequence: unit list entry, chunk slice and right-hand-side tile
 struct Unit {
-  int blk, t0, nt, j0, bcta, N, nrows, ncols, nchunks;
+  int blk, t0, nt, j0, bcta, N, nrows, ncols, ks, kb, nchunks;
 };
 template <bool ADJ, int KC>
 __device__ __forceinline__ Unit unit_at(const TmaArgs& a, int u) {
   Unit w;
-  const int ui = u % a.nunits, rt = u / a.nunits;
+  const int per = a.nunits * a.ksplit;
+  const int rt = u / per, rem = u - rt * per;
+  w.ks = rem / a.nunits;
+  const int ui = rem - w.ks * a.nunits;
   const int4 e = a.units[ui];
   w.blk = e.x;
   w.t0 = e.y;
@@ -127,7 +142,10 @@ __device__ __forceinline__ Unit unit_at(const TmaArgs& a, int u) {
   const int2 d = a.dims[w.blk];
   w.nrows = ADJ ? d.y : d.x;
   w.ncols = ADJ ? d.x : d.y;
-  w.nchunks = (w.ncols + KC - 1) / KC;
+  const int nch = (w.ncols + KC - 1) / KC;          // chunks of the block
+  const int cps = (nch + a.ksplit - 1) / a.ksplit;  // chunks per slice
+  w.kb = min(nch, w.ks * cps);
+  w.nchunks = min(nch, w.kb + cps) - w.kb;          // may be 0: the slice then stores zeros
   return w;
 }
 
@@ -138,10 +156,11 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
   using namespace tc;
   using namespace tma;
   using C = Cfg<MODE>;
-  constexpr int SA = C::SA, SB = C::SB, KC = C::KC;
+  constexpr int SB = C::SB, KC = C::KC;
   constexpr bool BF16 = C::BF16, X3 = C::X3;
+  const int SA = a.sa;
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t a_full[SA], a_ready[SA], a_empty[SA];
+  __shared__ __align__(8) uint64_t a_full[kMaxSA], a_ready[kMaxSA], a_empty[kMaxSA];
   __shared__ __align__(8) uint64_t b_full[SB], b_empty[SB];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], s_done;
   extern __shared__ __align__(16) uint8_t smem_dyn[];
@@ -149,12 +168,14 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
   uint8_t* gbase = smem_dyn + (base - su32(smem_dyn));
   const uint32_t TB = (uint32_t)a.nmax * 128;            // one B tile (N rows x 128 bytes)
   const uint32_t BSTAGE = (X3 ? 2u : 1u) * TB;           // split mode: head tile + tail tile
-  const uint32_t OFF_B = SA * C::ASTAGE, OFF_X = OFF_B + SB * BSTAGE;
+  // layout: A ring (SA x 16 KB), tail ring (split mode), B ring, x staging
+  const uint32_t OFF_L = (uint32_t)SA * kATile;
+  const uint32_t OFF_B = OFF_L + (X3 ? kSL * kATile : 0u), OFF_X = OFF_B + SB * BSTAGE;
   const int sld = a.nmax / 2;                             // staging row length (complex)
   const uint32_t XSLOT = (uint32_t)(KC * sld * 8);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int total = a.nunits * a.nrhs_tiles;
+  const int total = a.nunits * a.ksplit * a.nrhs_tiles;
 
   if (warp == 0) tmem_alloc(&s_tmem, kTmemCols);
   if (tid == 0) {
@@ -201,8 +222,8 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
             const int nbox = min(kTcRows / kBoxRows, (left + kBoxRows - 1) / kBoxRows);
             expect_tx(&a_full[s], (uint32_t)nbox * (kATile / (kTcRows / kBoxRows)));
             for (int q = 0; q < nbox; ++q)
-              tma_load_2d(base + s * C::ASTAGE + q * (kATile / (kTcRows / kBoxRows)), &amap, k * 64 / (BF16 ? 1 : 2),
-                          row0 + t * kTcRows + q * kBoxRows, &a_full[s], pol);
+              tma_load_2d(base + s * kATile + q * (kATile / (kTcRows / kBoxRows)), &amap,
+                          (w.kb + k) * 64 / (BF16 ? 1 : 2), row0 + t * kTcRows + q * kBoxRows, &a_full[s], pol);
           }
         }
       }
@@ -239,14 +260,15 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
               break;
             }
             fence_after();
-            const uint32_t sA = base + s * C::ASTAGE;
+            const uint32_t sA = base + s * kATile;
+            const uint32_t sL = base + OFF_L + (ia % kSL) * kATile;  // split mode: tail tile
             const uint32_t d = tmem + buf * kBufCols + (uint32_t)(t * w.N);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const uint32_t acc = (k > 0 || q > 0) ? 1u : 0u;
               if (X3) {
                 // small terms first: A_tail B_head, A_head B_tail, then A_head B_head
-                mma<false>(d, sdesc(sA + kATile + 32 * q), sdesc(sB + 32 * q), id, acc);
+                mma<false>(d, sdesc(sL + 32 * q), sdesc(sB + 32 * q), id, acc);
                 mma<false>(d, sdesc(sA + 32 * q), sdesc(sB + TB + 32 * q), id, 1u);
                 mma<false>(d, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, 1u);
               } else {
@@ -269,32 +291,59 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
     // The 128 threads walk the CTA's (unit, chunk) sequence in lockstep: every iteration starts
     // with a barrier that also ANDs their flags, so they stop together after a failed wait.
     const int et = tid - 64;
-    int fu = blockIdx.x, fk = 0;  // cursor of the chunk being fetched (two ahead)
+    // the gather of a chunk in two steps: pf_load reads the chunk's gather indices into registers
+    // (advancing the fetch cursor past units without chunks), pf_issue -- one expansion later,
+    // so that the index loads are long done -- issues the 16-byte copies into a staging slot
+    int fu = blockIdx.x, fk = 0;  // fetch cursor: unit and chunk of the next pf_load
     Unit fw{};
     if (fu < total) fw = unit_at<ADJ, KC>(a, fu);
-    auto fetch = [&](uint32_t slot) {
+    int pf_idx[kMaxPf];
+    int pf_cpr = 0, pf_j0 = 0;
+    bool pf_live = false;
+    auto pf_load = [&]() {
       while (fu < total && fk >= fw.nchunks) {  // skip units without chunks
         fu += gridDim.x;
         fk = 0;
         if (fu < total) fw = unit_at<ADJ, KC>(a, fu);
       }
-      if (fu < total) {
-        const int* cidx = a.colidx + (size_t)fw.blk * a.lcol;
-        const int cpr = fw.bcta >> 1;  // 16-byte copies per gathered row
-        const uint32_t dst = base + OFF_X + slot * XSLOT;
-        for (int e = et; e < KC * cpr; e += 128) {
-          const int c = e / cpr, q = e - c * cpr;
-          const int col = fk * KC + c;
-          const int idx = col < fw.ncols ? cidx[col] : -1;
-          const void* src = idx >= 0 ? (const void*)(a.x + (long long)idx * a.xrs + fw.j0 + 2 * q) : (const void*)a.x;
-          cp16(dst + (uint32_t)((c * sld + 2 * q) * 8), src, idx >= 0 ? 16 : 0);
+      pf_live = fu < total;
+      if (!pf_live) return;
+      const int* cidx = a.colidx + (size_t)fw.blk * a.lcol;
+      pf_cpr = fw.bcta >> 1;  // 16-byte copies per gathered row
+      pf_j0 = fw.j0;
+#pragma unroll
+      for (int m = 0; m < kMaxPf; ++m) {
+        const int e = et + 128 * m;
+        int idx = -1;
+        if (e < KC * pf_cpr) {
+          const int col = (fw.kb + fk) * KC + e / pf_cpr;
+          if (col < fw.ncols) idx = cidx[col];
         }
-        ++fk;
+        pf_idx[m] = idx;
+      }
+      ++fk;
+    };
+    auto pf_issue = [&](uint32_t slot) {
+      if (pf_live) {
+        const uint32_t dst = base + OFF_X + slot * XSLOT;
+#pragma unroll
+        for (int m = 0; m < kMaxPf; ++m) {
+          const int e = et + 128 * m;
+          if (e < KC * pf_cpr) {
+            const int c = e / pf_cpr, q = e - c * pf_cpr;
+            const int idx = pf_idx[m];
+            const void* src = idx >= 0 ? (const void*)(a.x + (long long)idx * a.xrs + pf_j0 + 2 * q) : (const void*)a.x;
+            cp16(dst + (uint32_t)((c * sld + 2 * q) * 8), src, idx >= 0 ? 16 : 0);
+          }
+        }
       }
       cp_commit();
     };
-    fetch(0);
-    fetch(1);
+    pf_load();
+    pf_issue(0);
+    pf_load();
+    pf_issue(1);
+    pf_load();
     uint32_t ia = 0, ib = 0;
     int u = blockIdx.x, k = 0;  // cursor of the chunk being expanded
     Unit w{};
@@ -311,7 +360,8 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
         ok = false;
         break;
       }
-      fetch((ib + 2) % kSX);
+      pf_issue((ib + 2) % kSX);  // chunk ib + 2, its indices loaded one iteration ago
+      pf_load();                 // indices of chunk ib + 3, in flight during the expansion
       const int sb = (int)(ib % SB);
       if (ib >= (uint32_t)SB) ok = mbar_wait(&b_empty[sb], ((ib / SB) - 1) & 1);
       if (ok) {
@@ -354,14 +404,22 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
         for (int t = 0; t < w.nt; ++t, ++ia) {
           const int s = (int)(ia % SA);
           if (ok) ok = mbar_wait(&a_full[s], (ia / SA) & 1);
+          // the tail slot was last used by tile ia - kSL: its MMAs are done when that tile's A
+          // slot was released (the release of slot (ia - kSL) % SA cannot have moved on since:
+          // its next use is a tile this loop has not split yet)
+          if (ok && ia >= (uint32_t)kSL) {
+            const uint32_t ip = ia - kSL;
+            ok = mbar_wait(&a_empty[ip % SA], (ip / SA) & 1);
+          }
           if (!ok) continue;
-          uint8_t* pA = gbase + s * C::ASTAGE;
+          uint8_t* pA = gbase + s * kATile;
+          uint8_t* pL = gbase + OFF_L + (ia % kSL) * kATile;
           for (int e = et; e < (int)(kATile / 16); e += 128) {
             float4* h = reinterpret_cast<float4*>(pA + 16 * e);
             const float4 v = *h;
             const float4 hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
             *h = hi;
-            *reinterpret_cast<float4*>(pA + kATile + 16 * e) =
+            *reinterpret_cast<float4*>(pL + 16 * e) =
                 make_float4(tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z), tf32_rna(v.w - hi.w));
           }
           fence_async_smem();
@@ -375,7 +433,8 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
   } else {
     // ---- epilogue: tensor memory -> scattered output rows -------------------------------------
     const int quad = warp & 3;  // TMEM lane quadrant this warp may read
-    const bool vec_store = a.ycs == 1 && (a.yrs & 1) == 0 && ((uintptr_t)a.y & 15) == 0;
+    const bool to_part = a.part != nullptr;
+    const bool vec_store = to_part || (a.ycs == 1 && (a.yrs & 1) == 0 && ((uintptr_t)a.y & 15) == 0);
     uint32_t v = 0;
     for (int u = blockIdx.x; u < total && ok; u += gridDim.x, ++v) {
       const Unit w = unit_at<ADJ, KC>(a, u);
@@ -390,7 +449,9 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
       for (int t = 0; t < w.nt; ++t) {
         const int row = (w.t0 + t) * kTcRows + quad * 32 + lane;
         const int oidx = row < w.nrows ? ridx[row] : -1;
-        float2* yr = a.y + (long long)(oidx < 0 ? 0 : oidx) * a.yrs;
+        // destination row: the output row, or this slice's partial row of the block row
+        float2* yr = to_part ? a.part + ((long long)w.ks * a.prow + (long long)w.blk * a.rows_per_blk + row) * a.b
+                             : a.y + (long long)(oidx < 0 ? 0 : oidx) * a.yrs;
         for (int cb = 0; cb < w.N; cb += 16) {
           uint32_t r[16];
           if (w.nchunks > 0) {
@@ -411,7 +472,8 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
 #pragma unroll
               for (int q = 0; q < 8; ++q)
                 if (jb + q < w.bcta)
-                  yr[(long long)(w.j0 + jb + q) * a.ycs] = make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+                  yr[(long long)(w.j0 + jb + q) * (to_part ? 1 : a.ycs)] =
+                      make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
             }
           }
         }
@@ -425,6 +487,25 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
   fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// The slices of a split in-place stage summed in slice order, written into the work vector W at
+// the block rows' own indices (the in-place stage's copy-back): W[idx[r]][j] = sum_ks part[ks][r][j]
+// for every packed row r of the stage with idx[r] >= 0 (the blocks' index sets are disjoint).
+__global__ void k_partial_reduce(const float2* part, int ksplit, long long prow, int b, const int* idx, float2* W) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= prow * b) return;
+  const long long r = t / b;
+  const int j = (int)(t - r * b);
+  const int row = idx[r];
+  if (row < 0) return;
+  float2 acc = part[t];
+  for (int q = 1; q < ksplit; ++q) {
+    const float2 v = part[(long long)q * prow * b + t];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  W[(long long)row * b + j] = acc;
 }
 
 }  // namespace fio
