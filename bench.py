@@ -44,12 +44,24 @@ HBM_FALLBACK_GBS = 6800.0
 FP32_LANES = 128  # FP32 FMA lanes per SM (nominal; the roofline uses the measured rate)
 
 
-def measured_traffic():
-    """DRAM bytes per apply of the stage kernel from the committed ncu summary, or None when the
+# headline precision: name -> (fio precision, dtype string, description, stage kernel source)
+PRECISIONS = {
+    "fp32": ("FIO_P32", "f32", "FP32 arithmetic on the CUDA cores", "fio_kernels.cuh"),
+    "split_tf32": ("FIO_PTF32X3", "tf32x3",
+                   "split-TF32 tensor-core products (head x head + head x tail + tail x head, FP32 accumulation)",
+                   "fio_tma.cuh"),
+    "tf32": ("FIO_PTF32", "tf32", "TF32 tensor-core products, FP32 accumulation", "fio_tma.cuh"),
+    "bf16": ("FIO_PBF16", "bf16", "BF16 tensor-core products, FP32 accumulation", "fio_tma.cuh"),
+}
+
+
+def measured_traffic(precision="fp32"):
+    """DRAM bytes per apply of the stage kernels from the committed ncu summary, or None when the
     kernel source changed since the counters were taken (the summary records its hash)."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "traffic_ex3_n256_b32.md")
-    src = os.path.join(ROOT, "paper_2105_02995_gb300", "csrc", "fio_kernels.cuh")
+    name = "traffic_ex3_n256_b32.md" if precision == "fp32" else f"traffic_ex3_n256_b32_{precision}.md"
+    prof = os.path.join(ROOT, "profiles", name)
+    src = os.path.join(ROOT, "paper_2105_02995_gb300", "csrc", PRECISIONS[precision][3])
     try:
         text = open(prof).read()
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -190,7 +202,9 @@ def config_of(a, info, l2):
     N = grid_size(a)
     size = f"n={a.n} (N={N})" if a.kind == "ex3" else f"N={N}"
     return {"workload": f"{OPERATORS.get(a.kind, a.kind)}, {size}, direct "
-                        f"inverse apply f = G K* u, complex64 (FP32 arithmetic), b={a.b} RHS per step",
+                        f"inverse apply f = G K* u, complex64 vectors ({PRECISIONS[a.precision][2]}), "
+                        f"b={a.b} RHS per step",
+            "precision": a.precision,
             "kind": a.kind, "n": a.n, "N": N, "b": a.b, "eps_bf": a.eps_bf, "eps_hif": a.eps_hif,
             "L": info.get("L"), "LH": info.get("LH"), "root": info.get("root"), "l2": l2,
             "parallelism": "replicas"}
@@ -269,6 +283,8 @@ def main():
     ap.add_argument("--eps-hif", type=float, default=1e-3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in tile shapes")
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
+                    help="arithmetic of the timed apply (complex64 vectors)")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
     ws, rank, local = dist_init()
@@ -294,6 +310,7 @@ def main():
     u = binding.colmajor(torch.from_numpy(u_np.astype(np.complex64)).cuda())
     f = binding.colmajor(torch.empty_like(u))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    hp = getattr(binding, PRECISIONS[a.precision][0])  # the timed apply's precision
 
     # autotuner: every stage launch's tile shape picked by timing, for the batches timed below
     # (FP32 headline and inner corrections, double-float residuals, and the FP64 b = 1 plain path)
@@ -312,12 +329,12 @@ def main():
         tuned["seconds"] = round(time.perf_counter() - t0, 2)
 
     for _ in range(a.warmup):
-        op.apply_inv(u, f)
+        op.apply_inv(u, f, precision=hp)
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
     clocks.start()
-    op.apply_inv(u, f)  # one more untimed step after the sampler has started
+    op.apply_inv(u, f, precision=hp)  # one more untimed step after the sampler has started
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
@@ -328,7 +345,7 @@ def main():
     for k in range(a.steps):
         flush.fill_(float(k))
         ev[k][0].record(stream)
-        op.apply_inv(u, f)
+        op.apply_inv(u, f, precision=hp)
         ev[k][1].record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
@@ -360,9 +377,9 @@ def main():
     prof = []
     for k in range(max(3, min(a.steps, 10))):
         flush.fill_(float(k))
-        prof.append(op.apply_profiled("inv", u, f))
+        prof.append(op.apply_profiled("inv", u, f, precision=hp))
     per = [statistics.mean(p[i] for p in prof) for i in range(len(prof[0]))]
-    es = 8  # complex64 bytes
+    es = 4 if a.precision == "bf16" else 8  # bytes per complex factor entry read by the kernels
     kern_time = kern_flops = kern_bytes = 0.0
     stage_rows = []
     for (lab, sd), t in zip(groups, per):
@@ -384,24 +401,39 @@ def main():
     pck = pclk.stop()
     nominal = nsm * FP32_LANES * 2 * (pck.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
     achieved = kern_flops / (kern_time / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
-            "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
-            "traffic": measured_traffic() if (a.n == 256 and b == 32 and a.kind == "ex3") else None,
-            "traffic_unit": "DRAM bytes per apply (all stage launches), ncu",
-            "kernel": "stage kernels k_stage_mm_vt / k_stage_mm_pipe (every stage launch of one apply, "
-                      "complex64, b=32, autotuned shapes)",
-            "algorithmic_bytes_per_apply": int(kern_bytes),
-            "peak_source": f"measured: FFMA-chain kernel (fio_probe_fp32) on {nsm} SMs, {fp32_probe_ms:.2f} ms per "
-                           f"launch, SM clock median {pck.get('sm_mhz')} MHz (max {pck.get('sm_max_mhz')}); nominal "
-                           f"{nsm} SMs x {FP32_LANES} lanes x 2 flop x max clock = {nominal:.1f}",
-            "hbm_view": {"achieved_gbs": round(kern_bytes / (kern_time / 1e3) / 1e9, 1),
-                         "peak_gbs": peaks.get("hbm_gbs"), "peak_source": src},
-            "stage_ms_sum": round(kern_time, 4), "step_ms": round(ms, 4)}
+    hbm_peak = peaks.get("hbm_gbs") or HBM_FALLBACK_GBS
+    achieved_gbs = kern_bytes / (kern_time / 1e3) / 1e9
+    # the apply's HBM floor (factors read once, u read and f written once): s (P_K + 2 P_G) + 2 s N b
+    floor_bytes = es * (tot["P_K"] + 2 * tot["P_G"]) + 2 * 8 * N * b
+    alu_view = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak, 4),
+                "peak_source": f"measured: FFMA-chain kernel (fio_probe_fp32) on {nsm} SMs, {fp32_probe_ms:.2f} ms "
+                               f"per launch, SM clock median {pck.get('sm_mhz')} MHz (max {pck.get('sm_max_mhz')}); "
+                               f"nominal {nsm} SMs x {FP32_LANES} lanes x 2 flop x max clock = {nominal:.1f}"}
+    hbm_view = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved_gbs / hbm_peak, 4), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+    main_view = alu_view if a.precision == "fp32" else hbm_view
+    roof = dict(main_view)
+    roof.update({
+        "traffic": measured_traffic(a.precision) if (a.n == 256 and b == 32 and a.kind == "ex3") else None,
+        "traffic_unit": "DRAM bytes per apply (all stage launches), ncu",
+        "kernel": ("stage kernels k_stage_mm_vt / k_stage_mm_pipe" if a.precision == "fp32" else
+                   "stage kernels k_stage_tma (TMA-fed tcgen05) and k_stage_tc") +
+                  f" (every stage launch of one apply, complex64 vectors, b={b}, autotuned variants)",
+        "algorithmic_bytes_per_apply": int(kern_bytes),
+        "algorithmic_bytes_definition": "per stage launch: factor entries read once + its input and output "
+                                        "vectors (s nnz + s b (in_len + out_len))",
+        "other_view": hbm_view if a.precision == "fp32" else alu_view,
+        "apply_floor": {"bytes": int(floor_bytes), "definition": "s (P_K + 2 P_G) + 2 s N b",
+                        "floor_ms": round(floor_bytes / hbm_peak / 1e6, 4),
+                        "frac_of_step": round(floor_bytes / hbm_peak / 1e6 / ms, 4)},
+        "stage_ms_sum": round(kern_time, 4), "step_ms": round(ms, 4)})
 
     # tensor-core stage products (tcgen05: TF32 / BF16 operands, and split TF32 at FP32 accuracy;
-    # FP32 accumulation), same timing; rel_diff_vs_fp32 = ||f_variant - f_fp32|| / ||f_fp32||
+    # FP32 accumulation) and the FP32 CUDA cores, same timing; rel_diff_vs_headline =
+    # ||f_variant - f_headline|| / ||f_headline||
     variants = {}
-    f_fp32 = f.clone()
+    f_head = f.clone()
     # the FP64 apply of the same (complex64-valued) right-hand sides: the reference for the error
     # of every complex64 result (the FP64 path agrees with the oracle's product of the same
     # factors to 1e-12 in the parity tests)
@@ -411,14 +443,16 @@ def main():
     def err64(x):
         return float("%.3g" % float(torch.linalg.norm(x.to(torch.complex128) - f_ref) / torch.linalg.norm(f_ref)))
 
-    fp32_err = err64(f_fp32)
-    for name, prec in (("tf32_tensor_core", binding.FIO_PTF32), ("bf16_tensor_core", binding.FIO_PBF16),
-                       ("split_tf32_tensor_core", binding.FIO_PTF32X3)):
+    head_err = err64(f_head)
+    for name, prec in (("fp32_cuda_cores", binding.FIO_P32), ("tf32_tensor_core", binding.FIO_PTF32),
+                       ("bf16_tensor_core", binding.FIO_PBF16), ("split_tf32_tensor_core", binding.FIO_PTF32X3)):
+        if prec == hp:
+            continue
         try:
             for _ in range(3):
                 op.apply_inv(u, f, precision=prec)
             torch.cuda.synchronize()
-            vdiff = float(torch.linalg.norm(f - f_fp32) / torch.linalg.norm(f_fp32))
+            vdiff = float(torch.linalg.norm(f - f_head) / torch.linalg.norm(f_head))
             evv = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                    for _ in range(a.steps)]
             for k in range(a.steps):
@@ -429,7 +463,7 @@ def main():
             torch.cuda.synchronize()
             vms = allmax(ws, statistics.mean(s_.elapsed_time(e_) for s_, e_ in evv))
             variants[name] = {"value": round(ws * b * 1000.0 / vms, 2), "unit": "RHS/s", "ms_per_step": round(vms, 4),
-                              "rel_diff_vs_fp32": float("%.3g" % vdiff), "rel_err_vs_fp64": err64(f)}
+                              "rel_diff_vs_headline": float("%.3g" % vdiff), "rel_err_vs_fp64": err64(f)}
         except Exception as exc:  # reported, not hidden: the variant line says why it is missing
             variants[name] = {"error": str(exc)[:200]}
 
@@ -438,7 +472,7 @@ def main():
     try:
         fsol = binding.colmajor(torch.empty_like(u))
         for _ in range(3):
-            op.apply_inv(u, f)
+            op.apply_inv(u, f, precision=hp)
             op.apply_Finv(f, fsol)
         torch.cuda.synchronize()
         evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -446,7 +480,7 @@ def main():
         for k in range(a.steps):
             flush.fill_(float(k))
             evf[k][0].record(stream)
-            op.apply_inv(u, f)
+            op.apply_inv(u, f, precision=hp)
             evf[k][1].record(stream)
             op.apply_Finv(f, fsol)
             evf[k][2].record(stream)
@@ -549,11 +583,11 @@ def main():
     fh = torch.empty_like(uh).pin_memory()
     uh_np, fh_np = uh.numpy().T, fh.numpy().T  # (N, b) Fortran views
     for _ in range(2):
-        op.apply_inv_host(uh_np, fh_np)
+        op.apply_inv_host(uh_np, fh_np, precision=hp)
     barrier(ws)
     s = time.perf_counter()
     for _ in range(a.steps):
-        op.apply_inv_host(uh_np, fh_np)
+        op.apply_inv_host(uh_np, fh_np, precision=hp)
     e2e_ms = allmax(ws, 1000 * (time.perf_counter() - s) / a.steps)
     e2e = {"value": ws * b * 1000.0 / e2e_ms, "unit": "RHS/s", "h2d_bytes_per_step": N * b * 8,
            "d2h_bytes_per_step": N * b * 8, "ms_per_step": e2e_ms}
@@ -565,12 +599,12 @@ def main():
     if rank == 0:
         line = {"metric": metric_of(a), "value": round(value, 2), "unit": "RHS/s",
                 "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 4),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": PRECISIONS[a.precision][1],
                 "data": "synthetic", "config": config_of(a, info, "flushed before every step (256 MB write)"),
                 "rhs_N_per_s": round(value * N, 1), "wall_ms_per_step": round(1000 * t_wall / a.steps, 4),
                 "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
                 "cpu_baseline": cpu, "stages": stage_rows, "variants": variants, "solve_latency": solves,
-                "autotune": tuned, "rel_err_vs_fp64": fp32_err, "stage_errors_vs_fp64": stage_err,
+                "autotune": tuned, "rel_err_vs_fp64": head_err, "stage_errors_vs_fp64": stage_err,
                 "factors": {"P_K": tot["P_K"], "P_G": tot["P_G"], "padded_K": tot["padded_K"],
                             "padded_G": tot["padded_G"], "bytes_c64": 8 * (tot["padded_K"] + tot["padded_G"]),
                             "build_s": {k: info.get(k) for k in ("t_bf", "t_peel", "t_hif", "t_total")}}}

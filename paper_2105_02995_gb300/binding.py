@@ -253,8 +253,9 @@ class Operator:
             self.apply_inv(u, f, precision)
         return g
 
-    def apply_inv_host(self, u: np.ndarray, f: np.ndarray | None = None) -> np.ndarray:
-        """Host-buffer direct solve: numpy (N, b) Fortran-ordered complex128/complex64 arrays."""
+    def apply_inv_host(self, u: np.ndarray, f: np.ndarray | None = None, precision=None) -> np.ndarray:
+        """Host-buffer direct solve: numpy (N, b) Fortran-ordered complex128/complex64 arrays;
+        precision defaults to the dtype's (P64 / P32)."""
         u = np.asfortranarray(u)
         if u.ndim == 1:
             u = u[:, None]
@@ -268,6 +269,8 @@ class Operator:
             raise ValueError("complex128 or complex64 expected")
         if u.shape[0] != self.N or f.shape != u.shape or f.dtype != u.dtype or not f.flags.f_contiguous:
             raise ValueError("bad host arrays")
+        if precision is not None:
+            prec = precision
         _check(self._lib.fio_apply_inv_host(self.h, u.ctypes.data_as(ctypes.c_void_p),
                                             f.ctypes.data_as(ctypes.c_void_p), self.N, u.shape[1],
                                             dt, prec, _stream()), "fio_apply_inv_host")

@@ -595,8 +595,14 @@ bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
 // (k_stage_mm_vt): 9 <16,2,8> with 128 threads, 10 <16,2,4> with 256 threads.  Shapes 2..7, 9, 10
 // need the pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the
 // plain tiled kernel.
-constexpr int kTmaVariant = 30;       // the TMA-fed persistent tensor-core kernel (k_stage_tma)
-constexpr int kTmaSplitVariant = 31;  // the same, in-place stages split over the K dimension
+// the TMA-fed persistent tensor-core kernel (k_stage_tma): 30 units of as many row tiles as tensor
+// memory holds and the deepest A ring; 31 the same with in-place stages split over K; 32 units
+// sized for about eight per SM; 33 an A ring of at most six slots
+constexpr int kTmaVariant = 30;
+constexpr int kTmaSplitVariant = 31;
+constexpr int kTmaBalancedVariant = 32;
+constexpr int kTmaShallowVariant = 33;
+inline bool is_tma_variant(int v) { return v >= kTmaVariant && v <= kTmaShallowVariant; }
 inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : (b <= 32 ? 3 : 4))); }
 // candidates per bucket, the built-in choice first
 constexpr int kNCand = 6;
@@ -714,7 +720,8 @@ int num_sms() {
 // x must be the row-major work layout with 16-byte aligned rows (b even), and the stage's tensor
 // map must exist
 bool launch_tma(const Stage& st, bool adj, const float2* x, long long xrs, long long xcs, float2* y, long long yrs,
-                long long ycs, int b, cudaStream_t s, int ksplit = 1, float2* part = nullptr, int gsel = -1) {
+                long long ycs, int b, cudaStream_t s, int var = kTmaVariant, int ksplit = 1, float2* part = nullptr,
+                int gsel = -1) {
   const bool bf = g_tc_mode == kTcBF16;
   const int dir = adj ? 1 : 0;
   if (!st.tma_ok[dir][bf ? 1 : 0] || xcs != 1 || (xrs & 1) || (b & 1) || ((uintptr_t)x & 15) || b < 8) return false;
@@ -734,7 +741,8 @@ bool launch_tma(const Stage& st, bool adj, const float2* x, long long xrs, long 
   // persistent CTAs' walk ends evenly, else single tiles
   const int gmax = a.nmax <= (int)tma::kBufCols / 4 ? 2 : (a.nmax <= (int)tma::kBufCols / 2 ? 1 : 0);
   int g = gmax;
-  while (g > 0 && (long long)st.nunits[dir][g] * ksplit * a.nrhs_tiles < 8LL * num_sms()) --g;
+  if (var == kTmaBalancedVariant)
+    while (g > 0 && (long long)st.nunits[dir][g] * ksplit * a.nrhs_tiles < 8LL * num_sms()) --g;
   if (gsel >= 0) g = std::min(g, gsel);
   a.ksplit = ksplit;
   a.part = part;
@@ -753,7 +761,7 @@ bool launch_tma(const Stage& st, bool adj, const float2* x, long long xrs, long 
   // as many 16 KB A slots as the 227 KB of shared memory hold (at least the split mode's tail
   // ring of three)
   constexpr int kSmemMax = 227 * 1024 - 1024;  // minus the kernel's static barriers
-  a.sa = std::min(tma::kMaxSA, (kSmemMax - tma::smem_fixed(g_tc_mode, a.nmax)) / 16384);
+  a.sa = std::min(var == kTmaShallowVariant ? 6 : tma::kMaxSA, (kSmemMax - tma::smem_fixed(g_tc_mode, a.nmax)) / 16384);
   if (a.sa < tma::kSL) return false;
   const int need = tma::smem_bytes(g_tc_mode, a.nmax, a.sa);
   const CUtensorMap& map = st.tmap[dir][bf ? 1 : 0];
@@ -805,7 +813,7 @@ bool launch_tc(const Stage& st, bool adj, const float2* x, long long xrs, long l
   a.nmax = 2 * ((std::min(b, kTcMaxRhs) + 7) & ~7);
   a.stage_x = (xcs == 1 && xrs % 2 == 0 && b % 2 == 0 && ((uintptr_t)x & 15) == 0) ? 1 : 0;
   a.ncmax = adj ? (int)st.R : (int)st.C;  // gather list length per block (forward: in, adjoint: out)
-  if (var == kTmaVariant || var == kTmaSplitVariant) return launch_tma(st, adj, x, xrs, xcs, y, yrs, ycs, b, s);
+  if (is_tma_variant(var)) return launch_tma(st, adj, x, xrs, xcs, y, yrs, ycs, b, s, var);
   if (ncta == 0) return true;
   switch (g_tc_mode * 2 + (adj ? 1 : 0)) {
     case 2 * kTcTF32: return launch_tc_var<false, kTcTF32>(a, ncta, s, var);
@@ -901,7 +909,7 @@ bool inplace_split<float2>(const Stage& st, bool adj, float2* W, float2* P, long
   ks = std::min<long long>(ks, std::max(1, nch / 4));
   ks = (int)std::min<long long>(ks, pcap / prow);
   ks = std::max(1, std::min(ks, 64));
-  if (!launch_tma(st, adj, W, b, 1, nullptr, 0, 0, b, s, ks, P, 0)) return false;
+  if (!launch_tma(st, adj, W, b, 1, nullptr, 0, 0, b, s, kTmaVariant, ks, P, 0)) return false;
   const long long tot = prow * b;
   k_partial_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, ks, prow, b, st.out, W);
   return true;
@@ -1206,7 +1214,7 @@ float time_launch(F&& launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   return best;
 }
 
-constexpr int kTcCand[6] = {0, 20, 21, 22, kTmaVariant, kTmaSplitVariant};
+constexpr int kTcCand[8] = {0, 20, 21, 22, kTmaVariant, kTmaSplitVariant, kTmaBalancedVariant, kTmaShallowVariant};
 
 // tune every stage launch of one vector type at b right-hand sides; choices[] gets the variant
 // per (stage, direction) in stage order, forward before adjoint
@@ -1240,7 +1248,7 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
       if (st.nblk > 0) {
         const StageArgs<V> a = stage_args<V>(st, adj, X, b, 1, Y, b, 1, b);
         float tbest = -1.f;
-        const int ncand = tc ? 6 : kNCand;
+        const int ncand = tc ? 8 : kNCand;
         for (int k = 0; k < ncand; ++k) {
           const int var = tc ? kTcCand[k] : kCand[bucket][k];
           if (var <= 0 && !tc) break;
@@ -1294,8 +1302,7 @@ extern "C" int fio_set_variant(fio_op op, int b, int precision, int variant) {
   const bool tc = mode != 0 && b >= 8;
   int ti;
   if (tc) {
-    if (variant != 0 && (variant < 20 || variant > 22) && variant != kTmaVariant && variant != kTmaSplitVariant)
-      return FIO_EINVAL;
+    if (variant != 0 && (variant < 20 || variant > 22) && !is_tma_variant(variant)) return FIO_EINVAL;
     ti = 2 + mode;
   } else {
     ti = precision == FIO_P64 ? 0 : (precision == FIO_PDF ? 2 : 1);

@@ -410,7 +410,7 @@ def test_tensor_core_ring_matches_single_buffer(name, prec, b):
         rc, y = _tc_apply(op, fn, xd, b, prec)
         assert rc == 0
         ref[w] = y.clone()
-    for var in (20, 21, 22, 30):
+    for var in (20, 21, 22, 30, 32, 33):
         op.set_variant(b, prec, var)
         for w, fn, oref in (("K", lib.fio_apply_K, fa.apply_Kdot), ("Kadj", lib.fio_apply_Kadj, fa.apply_Kdot_adj),
                             ("inv", lib.fio_apply_inv, fa.apply_inv)):
@@ -460,7 +460,7 @@ def test_set_variant_rejects_unknown_variants():
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 9) == -1    # complex64-only tiles
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 8) == -1    # few-RHS kernel needs b <= 4
     assert lib.fio_set_variant(op.h, 16, binding.FIO_PTF32, 3) == -1  # tensor-core launch: 0, 20-22, 30
-    assert lib.fio_set_variant(op.h, 16, binding.FIO_PTF32, 32) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_PTF32, 34) == -1
     assert lib.fio_set_variant(op.h, 16, binding.FIO_PTF32, 31) == 0
     assert lib.fio_set_variant(op.h, 16, binding.FIO_PTF32, 30) == 0
     assert lib.fio_set_variant(op.h, 16, binding.FIO_PTF32, 0) == 0

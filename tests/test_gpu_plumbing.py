@@ -99,9 +99,9 @@ def test_host_buffer_entry_is_exact(b):
     (binding.FIO_P64, torch.complex128, list(range(1, 8))),
     (binding.FIO_PDF, torch.complex128, list(range(1, 8))),
     (binding.FIO_P32, torch.complex64, list(range(1, 8)) + [9, 10]),
-    (binding.FIO_PTF32, torch.complex64, [20, 21, 22, 30, 31]),
-    (binding.FIO_PBF16, torch.complex64, [20, 21, 22, 30, 31]),
-    (binding.FIO_PTF32X3, torch.complex64, [20, 21, 22, 30, 31])])
+    (binding.FIO_PTF32, torch.complex64, [20, 21, 22, 30, 31, 32, 33]),
+    (binding.FIO_PBF16, torch.complex64, [20, 21, 22, 30, 31, 32, 33]),
+    (binding.FIO_PTF32X3, torch.complex64, [20, 21, 22, 30, 31, 32, 33])])
 def test_every_kernel_variant_is_exact(prec, dtype, variants, b):
     op, P = get()
     x = int_inputs(P.N, b, 4000)

@@ -13,7 +13,7 @@ from paper_2105_02995_gb300.serving import poisson_requests
 
 
 def _args(**kw):
-    base = dict(kind="ex3", n=256, b=32, eps_bf=1e-4, eps_hif=1e-3)
+    base = dict(kind="ex3", n=256, b=32, eps_bf=1e-4, eps_hif=1e-3, precision="fp32")
     base.update(kw)
     return argparse.Namespace(**base)
 
@@ -26,6 +26,10 @@ def test_bench_names_its_workload():
     e2 = _args(kind="ex2b", n=65536, eps_bf=1e-7, eps_hif=1e-4)
     assert bench.grid_size(e2) == 65536
     assert "Example 2" in bench.config_of(e2, {}, "flushed")["workload"]
+    # the arithmetic of the timed apply is named in the workload and in the config
+    sp = bench.config_of(_args(precision="split_tf32"), {}, "flushed")
+    assert sp["precision"] == "split_tf32" and "split-TF32" in sp["workload"]
+    assert bench.PRECISIONS["split_tf32"][1] == "tf32x3"
 
 
 def test_bench_traffic_guard_follows_the_kernel_source():
