@@ -283,6 +283,8 @@ def main():
     ap.add_argument("--eps-hif", type=float, default=1e-3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in tile shapes")
+    ap.add_argument("--tight-eps-bf", type=float, default=0.0,
+                    help="also time refinement whose outer residual uses a butterfly built with this tolerance")
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
                     help="arithmetic of the timed apply (complex64 vectors)")
     a = ap.parse_args()
@@ -526,8 +528,10 @@ def main():
             its += [i for i, _, _ in infos]
             rr += [r for _, r, _ in infos]
         nb = make_u().shape[1] if make_u().dim() == 2 else 1
-        # the last solution's residual recomputed with the FP64 apply (outside the timed region)
-        ru = uu - op.apply_K(ff)
+        # the last solution's residual recomputed with the FP64 apply of the operator the solve
+        # was held to (outside the timed region)
+        rop = kw.get("residual_op") or op
+        ru = uu - rop.apply_K(ff)
         rr64 = float((torch.linalg.norm(ru, dim=0) / torch.linalg.norm(uu, dim=0)).max())
         lat.sort()
         sts = [st for _, _, st in infos]
@@ -555,6 +559,22 @@ def main():
             timed_solves(f"ir_split_tf32_inner_dfres_b{nb}", lambda: binding.colmajor(u_more[:, :nb].contiguous()),
                          3, method=binding.FIO_IR, inner=binding.FIO_PTF32X3, outer=binding.FIO_PDF)
         timed_solves(f"gmres_fp32_precond_b{b}", lambda: u128, 3, method=binding.FIO_GMRES, inner=binding.FIO_P32)
+        if a.tight_eps_bf > 0:
+            # the outer residual u - K-dot_tight f with a tighter butterfly of the same FIO (the
+            # corrections still come from this operator's G-dot K-dot*)
+            from paper_2105_02995_gb300.builder.__main__ import build_cached
+            t0 = time.perf_counter()
+            tbuf, tinfo = build_cached(a.kind, a.n, a.tight_eps_bf, a.eps_hif, verbose=rank == 0, butterfly_only=True)
+            tight = binding.Operator(tbuf, binding.FIO_MASK_P64 | binding.FIO_MASK_DF)
+            tight_build_s = time.perf_counter() - t0
+            for nb in (1, 16, 128):
+                timed_solves(f"ir_split_tf32_inner_dfres_tight_b{nb}",
+                             lambda: binding.colmajor(u_more[:, :nb].contiguous()), 3, method=binding.FIO_IR,
+                             inner=binding.FIO_PTF32X3, outer=binding.FIO_PDF, residual_op=tight)
+                solves[f"ir_split_tf32_inner_dfres_tight_b{nb}"].update(
+                    {"tight_eps_bf": a.tight_eps_bf, "tight_nnz": tinfo.get("nnz_bf"),
+                     "tight_build_s": round(tight_build_s, 1)})
+            tight.release()
     except Exception as exc:
         solves["error"] = str(exc)[:200]
     def converged(k):

@@ -39,9 +39,13 @@ def cache_dir() -> str:
     return d
 
 
-def build_cached(kind, n, eps_bf, eps_hif, gpu=False, threads=None, verbose=True, hif_rescale=False):
-    """Build (or reuse) an operator in a subprocess with single-threaded BLAS; returns (bytes, info)."""
-    key = f"{kind}_{n}_{eps_bf:g}_{eps_hif:g}{'_resc' if hif_rescale else ''}_{source_hash()}"
+def build_cached(kind, n, eps_bf, eps_hif, gpu=False, threads=None, verbose=True, hif_rescale=False,
+                 butterfly_only=False):
+    """Build (or reuse) an operator in a subprocess with single-threaded BLAS; returns (bytes, info).
+    butterfly_only: K-dot alone (no peeling, no HIF; e.g. the tight operator of a refinement's
+    residual)."""
+    key = (f"{kind}_{n}_{eps_bf:g}_{eps_hif:g}{'_resc' if hif_rescale else ''}{'_bf' if butterfly_only else ''}"
+           f"_{source_hash()}")
     path = os.path.join(cache_dir(), key + ".fio")
     meta = path + ".json"
     if not (os.path.exists(path) and os.path.exists(meta)):
@@ -54,6 +58,8 @@ def build_cached(kind, n, eps_bf, eps_hif, gpu=False, threads=None, verbose=True
             cmd.append("--gpu")
         if hif_rescale:
             cmd.append("--hif-rescale")
+        if butterfly_only:
+            cmd.append("--butterfly-only")
         # the build's progress goes to stderr: stdout of the caller stays free for its own output
         out = sys.stderr if verbose else subprocess.PIPE
         r = subprocess.run(cmd, env=env, stdout=out, stderr=out, text=True)
@@ -75,9 +81,24 @@ def main(argv=None):
     ap.add_argument("--out", required=True)
     ap.add_argument("--gpu", action="store_true")
     ap.add_argument("--hif-rescale", action="store_true", help="Cholesky-rescaled HIF skeletonization")
+    ap.add_argument("--butterfly-only", action="store_true", help="K-dot alone: no peeling, no HIF")
     a = ap.parse_args(argv)
     sys.path.insert(0, ROOT)
-    from paper_2105_02995_gb300.builder import build_operator
+    from paper_2105_02995_gb300.builder import build_butterfly_only, build_operator
+    if a.butterfly_only:
+        t = time.time()
+        buf, bf = build_butterfly_only(a.kind, a.n, a.eps_bf)
+        info = {"kind": a.kind, "n": a.n, "t_bf": time.time() - t, "t_peel": 0.0, "t_hif": 0.0,
+                "t_total": time.time() - t, "root": 0, "nnz_bf": int(sum(sum(M.size for M, _, _ in st.blocks) for st in bf)),
+                "nnz_hif": 0, "nbytes": len(buf), "butterfly_only": True, "eps_bf": a.eps_bf}
+        tmp = a.out + ".tmp"
+        with open(tmp, "wb") as fh:
+            fh.write(buf)
+        with open(a.out + ".json", "w") as fh:
+            json.dump(info, fh, default=str)
+        os.replace(tmp, a.out)
+        print(json.dumps(info), flush=True)
+        return
     mv = None
     if a.gpu:
         from paper_2105_02995_gb300 import binding, build as fbuild

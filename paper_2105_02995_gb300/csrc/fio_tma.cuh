@@ -20,10 +20,11 @@
 //     gather and the B expansion are done once per chunk for up to G row tiles;
 //   * warp roles: warp 0 issues the TMA loads; warp 1 issues the MMAs (one elected lane);
 //     warps 2-5 gather the chunk's x rows (16-byte cp.async, two chunks ahead, their gather
-//     indices loaded one chunk earlier still), expand them into the B tile and, in split-TF32
-//     mode, split the landed A tiles into head (in place) and tail (a ring of its own, so every A
-//     slot is a TMA target); warps 6-9 read the accumulators out of tensor memory and scatter the
-//     rows;
+//     indices loaded one chunk earlier still; every thread expands the entries it copied itself,
+//     so no barrier couples the 128 threads) and expand them into the B tile; warps 6-9 read the
+//     accumulators out of tensor memory and scatter the rows; in split-TF32 mode warps 10-13
+//     split the landed A tiles into head (in place) and tail (a ring of its own, so every A slot
+//     is a TMA target);
 //   * accumulators are double-buffered in tensor memory (2 x 256 columns: all of an SM's tensor
 //     memory, so one CTA per SM), so the epilogue of a unit overlaps the MMAs of the next.
 // Every wait is bounded by %globaltimer (kWaitNs); a role whose wait gives up stops, records the
@@ -64,7 +65,7 @@ struct TmaArgs {
 
 namespace tma {
 
-constexpr int kThreads = 320;
+constexpr int kThreads = 448;  // 14 warps: producer, MMA, 4 expanders, 4 epilogue, 4 splitters
 constexpr uint32_t kTmemCols = 512;  // two accumulator buffers of 256 columns
 constexpr uint32_t kBufCols = kTmemCols / 2;
 constexpr int kBoxRows = 32;         // rows per TMA box (four boxes fill one 128-row tile)
@@ -103,19 +104,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(cx), "r"(cy), "r"(tc::su32(bar)), "l"(policy)
       : "memory");
-}
-// named barrier over n threads that also ANDs a flag across them (all threads leave with the same
-// value, so a group can agree to stop before any of its threads would wait on a barrier that
-// others no longer reach); the non-aligned form allows warps that have not reconverged
-__device__ __forceinline__ bool group_and(int id, int n, bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbarrier.red.and.pred q, %2, %3, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n}"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(id), "r"(n)
-      : "memory");
-  return r != 0;
 }
 template <int N>
 __device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -288,17 +276,20 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
     __syncwarp();
   } else if (warp < 6) {
     // ---- x gather, B expansion (and the A split) --------------------------------------------
-    // The 128 threads walk the CTA's (unit, chunk) sequence in lockstep: every iteration starts
-    // with a barrier that also ANDs their flags, so they stop together after a failed wait.
+    // Each of the 128 threads owns pairs (gathered row c, right-hand sides 2q and 2q+1) of every
+    // chunk: it issues that pair's 16-byte copy into the staging slot and later expands those two
+    // entries into the B tile, so it only ever reads its own copies -- its own cp.async.wait_group
+    // is the only synchronisation the staging needs, and the threads run without a group barrier
+    // (a thread whose bounded wait gives up stops arriving; the MMA warp's wait then gives up too).
+    // The gather of a chunk takes two steps: pf_load reads the chunk's gather indices into
+    // registers, pf_issue -- one expansion later, so that the index loads are long done -- issues
+    // the copies; the copies run two chunks ahead of the expansion.
     const int et = tid - 64;
-    // the gather of a chunk in two steps: pf_load reads the chunk's gather indices into registers
-    // (advancing the fetch cursor past units without chunks), pf_issue -- one expansion later,
-    // so that the index loads are long done -- issues the 16-byte copies into a staging slot
     int fu = blockIdx.x, fk = 0;  // fetch cursor: unit and chunk of the next pf_load
     Unit fw{};
     if (fu < total) fw = unit_at<ADJ, KC>(a, fu);
     int pf_idx[kMaxPf];
-    int pf_cpr = 0, pf_j0 = 0;
+    int pf_half = 0, pf_cpr = 0, pf_j0 = 0;
     bool pf_live = false;
     auto pf_load = [&]() {
       while (fu < total && fk >= fw.nchunks) {  // skip units without chunks
@@ -309,15 +300,17 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
       pf_live = fu < total;
       if (!pf_live) return;
       const int* cidx = a.colidx + (size_t)fw.blk * a.lcol;
-      pf_cpr = fw.bcta >> 1;  // 16-byte copies per gathered row
+      pf_half = fw.N >> 2;     // pairs per gathered row (right-hand sides padded to 8)
+      pf_cpr = fw.bcta >> 1;   // pairs that hold data
       pf_j0 = fw.j0;
 #pragma unroll
       for (int m = 0; m < kMaxPf; ++m) {
-        const int e = et + 128 * m;
+        const int p = et + 128 * m;
         int idx = -1;
-        if (e < KC * pf_cpr) {
-          const int col = (fw.kb + fk) * KC + e / pf_cpr;
-          if (col < fw.ncols) idx = cidx[col];
+        if (p < KC * pf_half) {
+          const int c = p / pf_half, q = p - c * pf_half;
+          const int col = (fw.kb + fk) * KC + c;
+          if (q < pf_cpr && col < fw.ncols) idx = cidx[col];
         }
         pf_idx[m] = idx;
       }
@@ -328,12 +321,14 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
         const uint32_t dst = base + OFF_X + slot * XSLOT;
 #pragma unroll
         for (int m = 0; m < kMaxPf; ++m) {
-          const int e = et + 128 * m;
-          if (e < KC * pf_cpr) {
-            const int c = e / pf_cpr, q = e - c * pf_cpr;
-            const int idx = pf_idx[m];
-            const void* src = idx >= 0 ? (const void*)(a.x + (long long)idx * a.xrs + pf_j0 + 2 * q) : (const void*)a.x;
-            cp16(dst + (uint32_t)((c * sld + 2 * q) * 8), src, idx >= 0 ? 16 : 0);
+          const int p = et + 128 * m;
+          if (p < KC * pf_half) {
+            const int c = p / pf_half, q = p - c * pf_half;
+            if (q < pf_cpr) {
+              const int idx = pf_idx[m];
+              const void* src = idx >= 0 ? (const void*)(a.x + (long long)idx * a.xrs + pf_j0 + 2 * q) : (const void*)a.x;
+              cp16(dst + (uint32_t)((c * sld + 2 * q) * 8), src, idx >= 0 ? 16 : 0);
+            }
           }
         }
       }
@@ -348,28 +343,27 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
     int u = blockIdx.x, k = 0;  // cursor of the chunk being expanded
     Unit w{};
     if (u < total) w = unit_at<ADJ, KC>(a, u);
-    while (true) {
+    while (ok) {
       while (u < total && k >= w.nchunks) {
         u += gridDim.x;
         k = 0;
         if (u < total) w = unit_at<ADJ, KC>(a, u);
       }
       if (u >= total) break;
-      cp_wait_group<1>();
-      if (!group_and(1, 128, ok)) {  // chunk ib's rows have landed for all 128 threads
-        ok = false;
-        break;
-      }
+      cp_wait_group<1>();        // this thread's copies of chunk ib have landed
       pf_issue((ib + 2) % kSX);  // chunk ib + 2, its indices loaded one iteration ago
       pf_load();                 // indices of chunk ib + 3, in flight during the expansion
       const int sb = (int)(ib % SB);
       if (ib >= (uint32_t)SB) ok = mbar_wait(&b_empty[sb], ((ib / SB) - 1) & 1);
-      if (ok) {
-        uint8_t* pB = gbase + OFF_B + sb * BSTAGE;
-        const float2* pX = reinterpret_cast<const float2*>(gbase + OFF_X + (ib % kSX) * XSLOT);
-        const int bp = w.N >> 1;
-        for (int e = et; e < KC * bp; e += 128) {
-          const int c = e / bp, j = e - c * bp;
+      if (!ok) break;
+      uint8_t* pB = gbase + OFF_B + sb * BSTAGE;
+      const float2* pX = reinterpret_cast<const float2*>(gbase + OFF_X + (ib % kSX) * XSLOT);
+      const int half = w.N >> 2;
+      for (int p = et; p < KC * half; p += 128) {
+        const int c = p / half, q = p - c * half;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = 2 * q + h;
           const float2 v = j < w.bcta ? pX[c * sld + j] : make_float2(0.f, 0.f);
           float p0, p1, q0, q1;
           if (!ADJ) {
@@ -395,42 +389,14 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
             *reinterpret_cast<float2*>(pB + swz(n1, ch) + off) = make_float2(q0, q1);
           }
         }
-        fence_async_smem();
-        mbar_arrive(&b_full[sb]);
       }
-      if (X3) {
-        // split every A tile of this chunk (one per row tile of the unit) once it has landed:
-        // head in place, tail into the second half of the stage (the same swizzled layout)
-        for (int t = 0; t < w.nt; ++t, ++ia) {
-          const int s = (int)(ia % SA);
-          if (ok) ok = mbar_wait(&a_full[s], (ia / SA) & 1);
-          // the tail slot was last used by tile ia - kSL: its MMAs are done when that tile's A
-          // slot was released (the release of slot (ia - kSL) % SA cannot have moved on since:
-          // its next use is a tile this loop has not split yet)
-          if (ok && ia >= (uint32_t)kSL) {
-            const uint32_t ip = ia - kSL;
-            ok = mbar_wait(&a_empty[ip % SA], (ip / SA) & 1);
-          }
-          if (!ok) continue;
-          uint8_t* pA = gbase + s * kATile;
-          uint8_t* pL = gbase + OFF_L + (ia % kSL) * kATile;
-          for (int e = et; e < (int)(kATile / 16); e += 128) {
-            float4* h = reinterpret_cast<float4*>(pA + 16 * e);
-            const float4 v = *h;
-            const float4 hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-            *h = hi;
-            *reinterpret_cast<float4*>(pL + 16 * e) =
-                make_float4(tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z), tf32_rna(v.w - hi.w));
-          }
-          fence_async_smem();
-          mbar_arrive(&a_ready[s]);
-        }
-      }
+      fence_async_smem();
+      mbar_arrive(&b_full[sb]);
       ++k;
       ++ib;
     }
     cp_wait_all();
-  } else {
+  } else if (warp < 10) {
     // ---- epilogue: tensor memory -> scattered output rows -------------------------------------
     const int quad = warp & 3;  // TMEM lane quadrant this warp may read
     const bool to_part = a.part != nullptr;
@@ -480,6 +446,39 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
       }
       fence_before();
       mbar_arrive(&acc_empty[buf]);
+    }
+  } else if (X3) {
+    // ---- split-TF32: every landed A tile split into head (in place) and tail (tail ring) -----
+    const int et = tid - 320;
+    uint32_t ia = 0;
+    for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+      const Unit w = unit_at<ADJ, KC>(a, u);
+      for (int k = 0; k < w.nchunks && ok; ++k) {
+        for (int t = 0; t < w.nt; ++t, ++ia) {
+          const int s = (int)(ia % SA);
+          ok = mbar_wait(&a_full[s], (ia / SA) & 1);
+          // the tail slot was last used by tile ia - kSL: its MMAs are done when that tile's A
+          // slot was released (that release cannot have moved on since: the slot's next use is a
+          // tile this loop has not split yet)
+          if (ok && ia >= (uint32_t)kSL) {
+            const uint32_t ip = ia - kSL;
+            ok = mbar_wait(&a_empty[ip % SA], (ip / SA) & 1);
+          }
+          if (!ok) break;
+          uint8_t* pA = gbase + s * kATile;
+          uint8_t* pL = gbase + OFF_L + (ia % kSL) * kATile;
+          for (int e = et; e < (int)(kATile / 16); e += 128) {
+            float4* hp = reinterpret_cast<float4*>(pA + 16 * e);
+            const float4 v = *hp;
+            const float4 hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+            *hp = hi;
+            *reinterpret_cast<float4*>(pL + 16 * e) =
+                make_float4(tf32_rna(v.x - hi.x), tf32_rna(v.y - hi.y), tf32_rna(v.z - hi.z), tf32_rna(v.w - hi.w));
+          }
+          fence_async_smem();
+          mbar_arrive(&a_ready[s]);
+        }
+      }
     }
   }
 
