@@ -758,12 +758,17 @@ bool launch_tma(const Stage& st, bool adj, const float2* x, long long xrs, long 
   const long long total = (long long)a.nunits * a.ksplit * a.nrhs_tiles;
   if (total == 0) return true;
   const int grid = (int)std::min<long long>(total, num_sms());
-  // as many 16 KB A slots as the 227 KB of shared memory hold (at least the split mode's tail
-  // ring of three)
-  constexpr int kSmemMax = 227 * 1024 - 1024;  // minus the kernel's static barriers
-  a.sa = std::min(var == kTmaShallowVariant ? 6 : tma::kMaxSA, (kSmemMax - tma::smem_fixed(g_tc_mode, a.nmax)) / 16384);
+  // shared memory (227 KB, minus the kernel's static barriers): the deepest x staging (gathers
+  // that miss L2 wait on HBM under the factor stream) that leaves at least six A slots, then as
+  // many 16 KB A slots as fit (at least the split mode's tail ring of three)
+  constexpr int kSmemMax = 227 * 1024 - 1024;
+  const int xs = tma::xslot_bytes(g_tc_mode, a.nmax), fixed = tma::smem_fixed(g_tc_mode, a.nmax);
+  const int amax = var == kTmaShallowVariant ? 6 : tma::kMaxSA;
+  a.sx = tma::kMaxSX;
+  while (a.sx > 3 && fixed + a.sx * xs + 6 * 16384 > kSmemMax) --a.sx;
+  a.sa = std::min(amax, (kSmemMax - fixed - a.sx * xs) / 16384);
   if (a.sa < tma::kSL) return false;
-  const int need = tma::smem_bytes(g_tc_mode, a.nmax, a.sa);
+  const int need = tma::smem_bytes(g_tc_mode, a.nmax, a.sa, a.sx);
   const CUtensorMap& map = st.tmap[dir][bf ? 1 : 0];
   switch (g_tc_mode * 2 + dir) {
 #define FIO_TMA_CASE(MODE, ADJ)                                                                   \

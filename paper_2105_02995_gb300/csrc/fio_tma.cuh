@@ -19,7 +19,7 @@
 //     tile, up to G tiles) sorted by size; all tiles of a unit share the chunk's B tile, so the x
 //     gather and the B expansion are done once per chunk for up to G row tiles;
 //   * warp roles: warp 0 issues the TMA loads; warp 1 issues the MMAs (one elected lane);
-//     warps 2-5 gather the chunk's x rows (16-byte cp.async, two chunks ahead, their gather
+//     warps 2-5 gather the chunk's x rows (16-byte cp.async, up to seven chunks ahead, their gather
 //     indices loaded one chunk earlier still; every thread expands the entries it copied itself,
 //     so no barrier couples the 128 threads) and expand them into the B tile; warps 6-9 read the
 //     accumulators out of tensor memory and scatter the rows; in split-TF32 mode warps 10-13
@@ -61,6 +61,7 @@ struct TmaArgs {
                       // part[(ks * prow + blk * rows_per_blk + r) * b + j] (summed by k_partial_reduce)
   long long prow;     // rows of one slice of `part` (nblk * rows_per_blk)
   int sa;             // A ring slots (1 .. kMaxSA), set by the launcher from the shared memory
+  int sx;             // x staging slots (3 .. kMaxSX): gathers run sx - 1 chunks ahead
 };
 
 namespace tma {
@@ -70,7 +71,7 @@ constexpr uint32_t kTmemCols = 512;  // two accumulator buffers of 256 columns
 constexpr uint32_t kBufCols = kTmemCols / 2;
 constexpr int kBoxRows = 32;         // rows per TMA box (four boxes fill one 128-row tile)
 constexpr uint32_t kATile = 16384;   // one 128 x 128-byte A tile
-constexpr int kSX = 3;               // x staging slots (gathered two chunks ahead)
+constexpr int kMaxSX = 8;            // x staging slots at most (gathers run up to 7 chunks ahead)
 constexpr int kMaxSA = 11;           // A ring slots at most
 constexpr int kSL = 3;               // split mode: slots of the tail tiles
 constexpr int kMaxPf = 8;            // gather copies per thread and chunk at most (KC x b / 2 / 128)
@@ -81,13 +82,15 @@ template <int MODE> struct Cfg {
   static constexpr int KC = BF16 ? 32 : 16;                 // complex columns per 128-byte chunk
 };
 
-// dynamic shared memory besides the A ring, for accumulator width nmax: alignment slack, tail
-// ring (split mode), B ring, x staging
+// dynamic shared memory besides the A ring and the x staging, for accumulator width nmax:
+// alignment slack, tail ring (split mode), B ring; and one x staging slot
 __host__ __device__ constexpr int smem_fixed(int mode, int nmax) {
-  return 1024 + (mode == kTcX3 ? kSL * 16384 : 0) + (mode == kTcX3 ? 2 * 2 : 3) * nmax * 128 +
-         kSX * (mode == kTcBF16 ? 32 : 16) * (nmax / 2) * 8;
+  return 1024 + (mode == kTcX3 ? kSL * 16384 : 0) + (mode == kTcX3 ? 2 * 2 : 3) * nmax * 128;
 }
-__host__ __device__ constexpr int smem_bytes(int mode, int nmax, int sa) { return smem_fixed(mode, nmax) + sa * 16384; }
+__host__ __device__ constexpr int xslot_bytes(int mode, int nmax) { return (mode == kTcBF16 ? 32 : 16) * (nmax / 2) * 8; }
+__host__ __device__ constexpr int smem_bytes(int mode, int nmax, int sa, int sx) {
+  return smem_fixed(mode, nmax) + sa * 16384 + sx * xslot_bytes(mode, nmax);
+}
 
 __device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::su32(bar)), "r"(bytes) : "memory");
@@ -107,6 +110,18 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 }
 template <int N>
 __device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// all but the newest n (0 .. kMaxSX - 2) commit groups of this thread have landed
+__device__ __forceinline__ void cp_wait_newest(int n) {
+  switch (n) {
+    case 0: cp_wait_group<0>(); break;
+    case 1: cp_wait_group<1>(); break;
+    case 2: cp_wait_group<2>(); break;
+    case 3: cp_wait_group<3>(); break;
+    case 4: cp_wait_group<4>(); break;
+    case 5: cp_wait_group<5>(); break;
+    default: cp_wait_group<6>(); break;
+  }
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 // work unit u of the CTA's sequence: unit list entry, chunk slice and right-hand-side tile
@@ -334,10 +349,11 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
       }
       cp_commit();
     };
-    pf_load();
-    pf_issue(0);
-    pf_load();
-    pf_issue(1);
+    const int SX = a.sx, D = SX - 1;  // gathers run D chunks ahead of the expansion
+    for (int q = 0; q < D; ++q) {
+      pf_load();
+      pf_issue((uint32_t)q);
+    }
     pf_load();
     uint32_t ia = 0, ib = 0;
     int u = blockIdx.x, k = 0;  // cursor of the chunk being expanded
@@ -350,14 +366,14 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
         if (u < total) w = unit_at<ADJ, KC>(a, u);
       }
       if (u >= total) break;
-      cp_wait_group<1>();        // this thread's copies of chunk ib have landed
-      pf_issue((ib + 2) % kSX);  // chunk ib + 2, its indices loaded one iteration ago
-      pf_load();                 // indices of chunk ib + 3, in flight during the expansion
+      cp_wait_newest(D - 1);     // this thread's copies of chunk ib have landed
+      pf_issue((ib + D) % SX);   // chunk ib + D, its indices loaded one iteration ago
+      pf_load();                 // indices of chunk ib + D + 1, in flight during the expansion
       const int sb = (int)(ib % SB);
       if (ib >= (uint32_t)SB) ok = mbar_wait(&b_empty[sb], ((ib / SB) - 1) & 1);
       if (!ok) break;
       uint8_t* pB = gbase + OFF_B + sb * BSTAGE;
-      const float2* pX = reinterpret_cast<const float2*>(gbase + OFF_X + (ib % kSX) * XSLOT);
+      const float2* pX = reinterpret_cast<const float2*>(gbase + OFF_X + (ib % SX) * XSLOT);
       const int half = w.N >> 2;
       for (int p = et; p < KC * half; p += 128) {
         const int c = p / half, q = p - c * half;
