@@ -597,7 +597,8 @@ bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
 // plain tiled kernel.
 // the TMA-fed persistent tensor-core kernel (k_stage_tma): 30 units of as many row tiles as tensor
 // memory holds and the deepest A ring; 31 the same with in-place stages split over K; 32 units
-// sized for about eight per SM; 33 an A ring of at most six slots
+// sized for about eight per SM; 33 an A ring of at most six slots (split TF32: a six-slot tail
+// ring instead of three)
 constexpr int kTmaVariant = 30;
 constexpr int kTmaSplitVariant = 31;
 constexpr int kTmaBalancedVariant = 32;
@@ -761,14 +762,18 @@ bool launch_tma(const Stage& st, bool adj, const float2* x, long long xrs, long 
   // shared memory (227 KB, minus the kernel's static barriers): the deepest x staging (gathers
   // that miss L2 wait on HBM under the factor stream) that leaves at least six A slots, then as
   // many 16 KB A slots as fit (at least the split mode's tail ring of three)
+  // split mode also keeps a tail ring: 3 slots, or 6 with variant 33 (a six-slot A ring otherwise)
   constexpr int kSmemMax = 227 * 1024 - 1024;
-  const int xs = tma::xslot_bytes(g_tc_mode, a.nmax), fixed = tma::smem_fixed(g_tc_mode, a.nmax);
-  const int amax = var == kTmaShallowVariant ? 6 : tma::kMaxSA;
-  a.sx = tma::kMaxSX;
+  const bool x3 = g_tc_mode == kTcX3;
+  a.sl = x3 ? (var == kTmaShallowVariant ? 6 : 3) : 2;
+  const int xs = tma::xslot_bytes(g_tc_mode, a.nmax);
+  const int fixed = tma::smem_fixed(g_tc_mode, a.nmax) + (x3 ? a.sl * 16384 : 0);
+  const int amax = (var == kTmaShallowVariant && !x3) ? 6 : tma::kMaxSA;
+  a.sx = x3 ? 4 : tma::kMaxSX;
   while (a.sx > 3 && fixed + a.sx * xs + 6 * 16384 > kSmemMax) --a.sx;
   a.sa = std::min(amax, (kSmemMax - fixed - a.sx * xs) / 16384);
-  if (a.sa < tma::kSL) return false;
-  const int need = tma::smem_bytes(g_tc_mode, a.nmax, a.sa, a.sx);
+  if (a.sa < 3) return false;
+  const int need = tma::smem_bytes(g_tc_mode, a.nmax, a.sa, a.sx, a.sl);
   const CUtensorMap& map = st.tmap[dir][bf ? 1 : 0];
   switch (g_tc_mode * 2 + dir) {
 #define FIO_TMA_CASE(MODE, ADJ)                                                                   \

@@ -319,16 +319,21 @@ __global__ void __launch_bounds__(128) k_stage_tc(TcArgs a) {
     __syncthreads();
     if (tid == 0) {
       fence_after();
+      if (X3) {
+        // small terms first: the four A_lo B_hi steps of the chunk, then per step A_hi B_lo and
+        // A_hi B_hi (the order of the TMA kernel, which releases the A_lo tile after its four)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (X3) {
-          // small terms first: A_lo B_hi, A_hi B_lo, then A_hi B_hi
+        for (int q = 0; q < 4; ++q)
           mma<false>(tmem, sdesc(sA + 16384 + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
           mma<false>(tmem, sdesc(sA + 32 * q), sdesc(sB + TB + 32 * q), id, 1u);
           mma<false>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, 1u);
-        } else {
-          mma<BF16>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
         }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          mma<BF16>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
       }
       mma_commit(&s_bar);
     }
@@ -492,15 +497,19 @@ __global__ void __launch_bounds__(192) k_stage_tc_ring(TcArgs a) {
         if (!ok) break;
         fence_after();
         const uint32_t sA = base + st * SB, sB = sA + TA;
+        if (X3) {  // the same order as k_stage_tc
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (X3) {
+          for (int q = 0; q < 4; ++q)
             mma<false>(tmem, sdesc(sA + 16384 + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
             mma<false>(tmem, sdesc(sA + 32 * q), sdesc(sB + TB + 32 * q), id, 1u);
             mma<false>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, 1u);
-          } else {
-            mma<BF16>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
           }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            mma<BF16>(tmem, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
         }
         mma_commit(&s_empty[st]);
       }

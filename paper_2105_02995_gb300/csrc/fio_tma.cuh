@@ -62,6 +62,7 @@ struct TmaArgs {
   long long prow;     // rows of one slice of `part` (nblk * rows_per_blk)
   int sa;             // A ring slots (1 .. kMaxSA), set by the launcher from the shared memory
   int sx;             // x staging slots (3 .. kMaxSX): gathers run sx - 1 chunks ahead
+  int sl;             // split mode: tail ring slots (2 .. kMaxSL)
 };
 
 namespace tma {
@@ -73,7 +74,7 @@ constexpr int kBoxRows = 32;         // rows per TMA box (four boxes fill one 12
 constexpr uint32_t kATile = 16384;   // one 128 x 128-byte A tile
 constexpr int kMaxSX = 8;            // x staging slots at most (gathers run up to 7 chunks ahead)
 constexpr int kMaxSA = 11;           // A ring slots at most
-constexpr int kSL = 3;               // split mode: slots of the tail tiles
+constexpr int kMaxSL = 6;            // split mode: slots of the tail tiles at most
 constexpr int kMaxPf = 8;            // gather copies per thread and chunk at most (KC x b / 2 / 128)
 
 template <int MODE> struct Cfg {
@@ -82,14 +83,14 @@ template <int MODE> struct Cfg {
   static constexpr int KC = BF16 ? 32 : 16;                 // complex columns per 128-byte chunk
 };
 
-// dynamic shared memory besides the A ring and the x staging, for accumulator width nmax:
-// alignment slack, tail ring (split mode), B ring; and one x staging slot
+// dynamic shared memory besides the A ring, the tail ring and the x staging, for accumulator
+// width nmax: alignment slack and the B ring; and one x staging slot
 __host__ __device__ constexpr int smem_fixed(int mode, int nmax) {
-  return 1024 + (mode == kTcX3 ? kSL * 16384 : 0) + (mode == kTcX3 ? 2 * 2 : 3) * nmax * 128;
+  return 1024 + (mode == kTcX3 ? 2 * 2 : 3) * nmax * 128;
 }
 __host__ __device__ constexpr int xslot_bytes(int mode, int nmax) { return (mode == kTcBF16 ? 32 : 16) * (nmax / 2) * 8; }
-__host__ __device__ constexpr int smem_bytes(int mode, int nmax, int sa, int sx) {
-  return smem_fixed(mode, nmax) + sa * 16384 + sx * xslot_bytes(mode, nmax);
+__host__ __device__ constexpr int smem_bytes(int mode, int nmax, int sa, int sx, int sl) {
+  return smem_fixed(mode, nmax) + (sa + (mode == kTcX3 ? sl : 0)) * 16384 + sx * xslot_bytes(mode, nmax);
 }
 
 __device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
   const int SA = a.sa;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t a_full[kMaxSA], a_ready[kMaxSA], a_empty[kMaxSA];
+  __shared__ __align__(8) uint64_t l_free[kMaxSL];  // split mode: a tail slot's MMAs are done
   __shared__ __align__(8) uint64_t b_full[SB], b_empty[SB];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], s_done;
   extern __shared__ __align__(16) uint8_t smem_dyn[];
@@ -173,7 +175,8 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
   const uint32_t BSTAGE = (X3 ? 2u : 1u) * TB;           // split mode: head tile + tail tile
   // layout: A ring (SA x 16 KB), tail ring (split mode), B ring, x staging
   const uint32_t OFF_L = (uint32_t)SA * kATile;
-  const uint32_t OFF_B = OFF_L + (X3 ? kSL * kATile : 0u), OFF_X = OFF_B + SB * BSTAGE;
+  const int SL = a.sl;
+  const uint32_t OFF_B = OFF_L + (X3 ? (uint32_t)SL * kATile : 0u), OFF_X = OFF_B + SB * BSTAGE;
   const int sld = a.nmax / 2;                             // staging row length (complex)
   const uint32_t XSLOT = (uint32_t)(KC * sld * 8);
 
@@ -195,6 +198,7 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
       mbar_init(&acc_full[q], 1);
       mbar_init(&acc_empty[q], 128);
     }
+    for (int q = 0; q < kMaxSL; ++q) mbar_init(&l_free[q], 1);
     mbar_init(&s_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&amap)) : "memory");
@@ -264,19 +268,24 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
             }
             fence_after();
             const uint32_t sA = base + s * kATile;
-            const uint32_t sL = base + OFF_L + (ia % kSL) * kATile;  // split mode: tail tile
+            const uint32_t sL = base + OFF_L + (ia % SL) * kATile;  // split mode: tail tile
             const uint32_t d = tmem + buf * kBufCols + (uint32_t)(t * w.N);
+            if (X3) {
+              // the tail tile's products first, committed on their own so that the tail slot is
+              // free for the next split as soon as they are done; then the head products
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const uint32_t acc = (k > 0 || q > 0) ? 1u : 0u;
-              if (X3) {
-                // small terms first: A_tail B_head, A_head B_tail, then A_head B_head
-                mma<false>(d, sdesc(sL + 32 * q), sdesc(sB + 32 * q), id, acc);
+              for (int q = 0; q < 4; ++q)
+                mma<false>(d, sdesc(sL + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
+              mma_commit(&l_free[ia % SL]);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
                 mma<false>(d, sdesc(sA + 32 * q), sdesc(sB + TB + 32 * q), id, 1u);
                 mma<false>(d, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, 1u);
-              } else {
-                mma<BF16>(d, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, acc);
               }
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                mma<BF16>(d, sdesc(sA + 32 * q), sdesc(sB + 32 * q), id, (k > 0 || q > 0) ? 1u : 0u);
             }
             mma_commit(&a_empty[s]);
           }
@@ -473,16 +482,11 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
         for (int t = 0; t < w.nt; ++t, ++ia) {
           const int s = (int)(ia % SA);
           ok = mbar_wait(&a_full[s], (ia / SA) & 1);
-          // the tail slot was last used by tile ia - kSL: its MMAs are done when that tile's A
-          // slot was released (that release cannot have moved on since: the slot's next use is a
-          // tile this loop has not split yet)
-          if (ok && ia >= (uint32_t)kSL) {
-            const uint32_t ip = ia - kSL;
-            ok = mbar_wait(&a_empty[ip % SA], (ip / SA) & 1);
-          }
+          // the tail slot was last used by tile ia - SL, whose tail products released it
+          if (ok && ia >= (uint32_t)SL) ok = mbar_wait(&l_free[ia % SL], ((ia / SL) - 1) & 1);
           if (!ok) break;
           uint8_t* pA = gbase + s * kATile;
-          uint8_t* pL = gbase + OFF_L + (ia % kSL) * kATile;
+          uint8_t* pL = gbase + OFF_L + (ia % SL) * kATile;
           for (int e = et; e < (int)(kATile / 16); e += 128) {
             float4* hp = reinterpret_cast<float4*>(pA + 16 * e);
             const float4 v = *hp;
