@@ -500,6 +500,29 @@ def main():
     except Exception as exc:
         variants["full_solve_u_eq_KFf"] = {"error": str(exc)[:200]}
 
+    # the tensor-core kernel variants stage by stage on this operator (every stage launch of the
+    # apply pinned to one variant at a time; CUDA events per launch group): what the autotuner
+    # weighs, for the headline's tensor-core precision
+    variant_ms = {}
+    if a.precision != "fp32":
+        try:
+            for var in (0, 20, 30, 31, 32, 33):
+                op.set_variant(b, hp, var)
+                for _ in range(2):
+                    op.apply_profiled("inv", u, f, precision=hp)
+                runs = []
+                for k in range(3):
+                    flush.fill_(float(k))
+                    runs.append(op.apply_profiled("inv", u, f, precision=hp))
+                variant_ms[str(var)] = [round(min(r[i] for r in runs), 4) for i in range(len(runs[0]))]
+            variant_ms["groups"] = [lab if sd is None else f"{lab}:{sd['role']}:{sd['level']}" for lab, sd in groups]
+        except Exception as exc:
+            variant_ms["error"] = str(exc)[:200]
+        finally:
+            op.set_variant(b, hp, 0)
+            if not a.no_autotune:
+                op.autotune(b, hp)  # restore the tuned choices
+
     # per-stage error of every precision against the FP64 path (8 right-hand sides: the
     # tensor-core precisions need b >= 8), in application order of the inverse apply
     stage_err = {}
@@ -624,7 +647,7 @@ def main():
                 "rhs_N_per_s": round(value * N, 1), "wall_ms_per_step": round(1000 * t_wall / a.steps, 4),
                 "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
                 "cpu_baseline": cpu, "stages": stage_rows, "variants": variants, "solve_latency": solves,
-                "autotune": tuned, "rel_err_vs_fp64": head_err, "stage_errors_vs_fp64": stage_err,
+                "autotune": tuned, "variant_stage_ms": variant_ms, "rel_err_vs_fp64": head_err, "stage_errors_vs_fp64": stage_err,
                 "factors": {"P_K": tot["P_K"], "P_G": tot["P_G"], "padded_K": tot["padded_K"],
                             "padded_G": tot["padded_G"], "bytes_c64": 8 * (tot["padded_K"] + tot["padded_G"]),
                             "build_s": {k: info.get(k) for k in ("t_bf", "t_peel", "t_hif", "t_total")}}}

@@ -604,6 +604,9 @@ constexpr int kTmaSplitVariant = 31;
 constexpr int kTmaBalancedVariant = 32;
 constexpr int kTmaShallowVariant = 33;
 inline bool is_tma_variant(int v) { return v >= kTmaVariant && v <= kTmaShallowVariant; }
+// with a tensor-core precision: this stage launch on the FP32 CUDA cores instead (at least as
+// accurate; the small blocks of the lowest HIF levels run faster there)
+constexpr int kFp32CoresVariant = 40;
 inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : (b <= 32 ? 3 : 4))); }
 // candidates per bucket, the built-in choice first
 constexpr int kNCand = 6;
@@ -886,9 +889,11 @@ void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long lon
   if (st.nblk == 0) return;
   if (use_tc<V>(st, b, adj)) {
     const int tv = st.var[2 + g_tc_mode][adj ? 1 : 0][rhs_bucket(b)];
-    if (!launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s, tv))
-      launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s, 0);
-    return;
+    if (tv != kFp32CoresVariant) {
+      if (!launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s, tv))
+        launch_tc(st, adj, (const float2*)x, xrs, xcs, (float2*)y, yrs, ycs, b, s, 0);
+      return;
+    }
   }
   const StageArgs<V> a = stage_args<V>(st, adj, x, xrs, xcs, y, yrs, ycs, b);
   const int var = st.var[type_index<V>()][adj ? 1 : 0][rhs_bucket(b)];
@@ -1224,7 +1229,8 @@ float time_launch(F&& launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   return best;
 }
 
-constexpr int kTcCand[8] = {0, 20, 21, 22, kTmaVariant, kTmaSplitVariant, kTmaBalancedVariant, kTmaShallowVariant};
+constexpr int kTcCand[9] = {0,  20, 21, 22, kTmaVariant, kTmaSplitVariant, kTmaBalancedVariant, kTmaShallowVariant,
+                            kFp32CoresVariant};
 
 // tune every stage launch of one vector type at b right-hand sides; choices[] gets the variant
 // per (stage, direction) in stage order, forward before adjoint
@@ -1258,7 +1264,7 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
       if (st.nblk > 0) {
         const StageArgs<V> a = stage_args<V>(st, adj, X, b, 1, Y, b, 1, b);
         float tbest = -1.f;
-        const int ncand = tc ? 8 : kNCand;
+        const int ncand = tc ? 9 : kNCand;
         for (int k = 0; k < ncand; ++k) {
           const int var = tc ? kTcCand[k] : kCand[bucket][k];
           if (var <= 0 && !tc) break;
@@ -1270,6 +1276,15 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
                 [&] {
                   st.var[ti][dir][bucket] = (int8_t)var;
                   inplace_stage<V>(st, adj, X, Y, b, s, (V*)bufs[2], op->max_len);
+                  return true;
+                },
+                s, e0, e1);
+          } else if (tc && var == kFp32CoresVariant) {
+            // the FP32 CUDA-core launch with its own tuned (or built-in) tile shape
+            t = time_launch(
+                [&] {
+                  if (adj) launch_stage_dir<V, true>(a, s, st.var[1][1][bucket]);
+                  else launch_stage_dir<V, false>(a, s, st.var[1][0][bucket]);
                   return true;
                 },
                 s, e0, e1);
@@ -1312,7 +1327,8 @@ extern "C" int fio_set_variant(fio_op op, int b, int precision, int variant) {
   const bool tc = mode != 0 && b >= 8;
   int ti;
   if (tc) {
-    if (variant != 0 && (variant < 20 || variant > 22) && !is_tma_variant(variant)) return FIO_EINVAL;
+    if (variant != 0 && (variant < 20 || variant > 22) && !is_tma_variant(variant) && variant != kFp32CoresVariant)
+      return FIO_EINVAL;
     ti = 2 + mode;
   } else {
     ti = precision == FIO_P64 ? 0 : (precision == FIO_PDF ? 2 : 1);

@@ -142,3 +142,15 @@ def plumbing_operator(seed: int = 11, N: int = 96):
     h2 = _inplace_stage(rng, N, [6, 7, 5], 9, 1, pool)
     root = _inplace_stage(rng, N, [18], 20, 1, pool)
     return hand_pack(N, [s1, s2, s3], [h1, h2], [root], roles=[1, 2])
+
+
+def plumbing_operator_large(seed: int = 12):
+    """A butterfly-only exact-integer operator with the block shapes of a 2D middle stage (1D,
+    N = 16384): 64 blocks of 398 x 256 live entries (N -> 25472) and back (64 blocks of 256 x 398),
+    so that a persistent kernel's CTAs each walk many work units.  Signed permutations with one
+    extra +-1 term per block: integer results, exact in every precision."""
+    rng = np.random.default_rng(seed)
+    N, mid = 16384, 64 * 398
+    s1 = _map_stage(rng, N, mid, 64, 400, 258, [398] * 64, [256] * 64, 1)
+    s2 = _map_stage(rng, mid, N, 64, 258, 400, [256] * 64, [398] * 64, 1)
+    return hand_pack(N, [s1, s2], [], [])

@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 from oracle import factor_apply as fa  # noqa: E402
 from paper_2105_02995_gb300 import binding, build as fbuild  # noqa: E402
 
-from handpack import plumbing_operator  # noqa: E402
+from handpack import plumbing_operator, plumbing_operator_large  # noqa: E402
 
 PRECS = [(binding.FIO_P64, torch.complex128), (binding.FIO_PDF, torch.complex128),
          (binding.FIO_P32, torch.complex64), (binding.FIO_PTF32, torch.complex64),
@@ -133,3 +133,34 @@ def test_few_rhs_kernel_is_exact():
                     assert np.array_equal(yd.cpu().numpy().astype(np.complex128), ref(P, x)), (prec, b, what)
             finally:
                 op.set_variant(b, prec, 0)
+
+
+_big = {}
+
+
+@pytest.mark.parametrize("prec", [binding.FIO_PTF32, binding.FIO_PBF16, binding.FIO_PTF32X3, binding.FIO_P32])
+@pytest.mark.parametrize("b", [8, 40, 72])
+def test_large_exact_operator_every_variant(prec, b):
+    """Blocks of 398 x 256 on 64 blocks (many work units per persistent CTA, partial row tiles,
+    several right-hand-side tiles): K-dot and K-dot* exact for every kernel variant; a mismatch
+    reports the rows and right-hand sides it touches."""
+    if "op" not in _big:
+        fbuild.build()
+        buf = plumbing_operator_large()
+        _big["op"] = (binding.Operator(buf), fa.PackedFactors(buf))
+    op, P = _big["op"]
+    x = int_inputs(P.N, b, 6000 + b)
+    xd = binding.colmajor(torch.from_numpy(x).to("cuda", torch.complex64))
+    want = {"K": fa.apply_Kdot(P, x), "Kadj": fa.apply_Kdot_adj(P, x)}
+    variants = list(range(1, 8)) + [9, 10] if prec == binding.FIO_P32 else [0, 20, 30, 31, 32, 33, 40]
+    try:
+        for var in variants:
+            op.set_variant(b, prec, var)
+            for what in ("K", "Kadj"):
+                yd = binding.colmajor(torch.empty((P.N, b), dtype=torch.complex64, device="cuda"))
+                run(op, what, xd, yd, b, P.N, prec)
+                got = yd.cpu().numpy().astype(np.complex128)
+                bad = np.argwhere(got != want[what])
+                assert bad.size == 0, (var, what, len(bad), np.unique(bad[:, 0])[:20], np.unique(bad[:, 1])[:20])
+    finally:
+        op.set_variant(b, prec, 0)
