@@ -300,20 +300,24 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
     __syncwarp();
   } else if (warp < 6) {
     // ---- x gather, B expansion (and the A split) --------------------------------------------
-    // Each of the 128 threads owns pairs (gathered row c, right-hand sides 2q and 2q+1) of every
-    // chunk: it issues that pair's 16-byte copy into the staging slot and later expands those two
-    // entries into the B tile, so it only ever reads its own copies -- its own cp.async.wait_group
-    // is the only synchronisation the staging needs, and the threads run without a group barrier
-    // (a thread whose bounded wait gives up stops arriving; the MMA warp's wait then gives up too).
+    // Each of the 128 threads owns pairs (gathered row c, right-hand sides 2q and 2q+1): pair
+    // p = c * HP + q with HP = nmax / 4 (the pairs of a full right-hand-side tile, the same for
+    // every unit of the launch, so that a thread owns the same staging entries whatever the
+    // unit's width) belongs to thread p mod 128.  It issues that pair's 16-byte copy into the
+    // staging slot and later expands those two entries into the B tile, so it only ever reads its
+    // own copies -- its own cp.async.wait_group is the only synchronisation the staging needs, and
+    // the threads run without a group barrier (a thread whose bounded wait gives up stops
+    // arriving; the MMA warp's wait then gives up too).
     // The gather of a chunk takes two steps: pf_load reads the chunk's gather indices into
     // registers, pf_issue -- one expansion later, so that the index loads are long done -- issues
     // the copies; the copies run two chunks ahead of the expansion.
     const int et = tid - 64;
+    const int HP = a.nmax >> 2;   // pairs per gathered row of a full right-hand-side tile
     int fu = blockIdx.x, fk = 0;  // fetch cursor: unit and chunk of the next pf_load
     Unit fw{};
     if (fu < total) fw = unit_at<ADJ, KC>(a, fu);
     int pf_idx[kMaxPf];
-    int pf_half = 0, pf_cpr = 0, pf_j0 = 0;
+    int pf_cpr = 0, pf_j0 = 0;
     bool pf_live = false;
     auto pf_load = [&]() {
       while (fu < total && fk >= fw.nchunks) {  // skip units without chunks
@@ -324,15 +328,14 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
       pf_live = fu < total;
       if (!pf_live) return;
       const int* cidx = a.colidx + (size_t)fw.blk * a.lcol;
-      pf_half = fw.N >> 2;     // pairs per gathered row (right-hand sides padded to 8)
       pf_cpr = fw.bcta >> 1;   // pairs that hold data
       pf_j0 = fw.j0;
 #pragma unroll
       for (int m = 0; m < kMaxPf; ++m) {
         const int p = et + 128 * m;
         int idx = -1;
-        if (p < KC * pf_half) {
-          const int c = p / pf_half, q = p - c * pf_half;
+        if (p < KC * HP) {
+          const int c = p / HP, q = p - c * HP;
           const int col = (fw.kb + fk) * KC + c;
           if (q < pf_cpr && col < fw.ncols) idx = cidx[col];
         }
@@ -346,8 +349,8 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
 #pragma unroll
         for (int m = 0; m < kMaxPf; ++m) {
           const int p = et + 128 * m;
-          if (p < KC * pf_half) {
-            const int c = p / pf_half, q = p - c * pf_half;
+          if (p < KC * HP) {
+            const int c = p / HP, q = p - c * HP;
             if (q < pf_cpr) {
               const int idx = pf_idx[m];
               const void* src = idx >= 0 ? (const void*)(a.x + (long long)idx * a.xrs + pf_j0 + 2 * q) : (const void*)a.x;
@@ -383,9 +386,10 @@ __global__ void __launch_bounds__(tma::kThreads, 1) k_stage_tma(const TmaArgs a,
       if (!ok) break;
       uint8_t* pB = gbase + OFF_B + sb * BSTAGE;
       const float2* pX = reinterpret_cast<const float2*>(gbase + OFF_X + (ib % SX) * XSLOT);
-      const int half = w.N >> 2;
-      for (int p = et; p < KC * half; p += 128) {
-        const int c = p / half, q = p - c * half;
+      const int half = w.N >> 2;  // pairs of this unit's right-hand-side tile (<= HP)
+      for (int p = et; p < KC * HP; p += 128) {
+        const int c = p / HP, q = p - c * HP;
+        if (q >= half) continue;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int j = 2 * q + h;
