@@ -531,24 +531,30 @@ void launch_pipe(StageArgs<V> a, cudaStream_t s) {
   k_stage_mm_pipe<V, ADJ, TX, TB, TR, CK><<<grid, 256, S::SMEM, s>>>(a);
 }
 
-// complex64 tiles with contiguous per-thread rows and right-hand sides (k_stage_mm_vt)
-template <bool ADJ, int TX, int TB, int TR, int NT>
-void launch_vt(StageArgs<float2> a, cudaStream_t s) {
-  using S = VtShape<ADJ, TX, TB, TR, NT>;
-  smem_opt_in((const void*)k_stage_mm_vt<ADJ, TX, TB, TR, NT>, S::SMEM);
-  static_assert(S::RT == kTileRows, "tile lists are built for 64-row tiles");
+// complex64 tiles with contiguous per-thread rows and right-hand sides (k_stage_mm_vt); 64- or
+// 128-row tiles (the latter from the stage's list of 128-row tiles)
+template <bool ADJ, int TX, int TB, int TR, int NT, int CK = 32>
+bool launch_vt(StageArgs<float2> a, cudaStream_t s) {
+  using S = VtShape<ADJ, TX, TB, TR, NT, CK>;
+  static_assert(S::RT == kTileRows || S::RT == 2 * kTileRows, "tile lists hold 64- and 128-row tiles");
+  if (S::RT != kTileRows) {
+    if (!a.tiles128) return false;
+    a.tiles = a.tiles128;
+    a.ntiles_list = a.ntiles128;
+  }
+  if (!smem_opt_in((const void*)k_stage_mm_vt<ADJ, TX, TB, TR, NT, CK>, S::SMEM)) return false;
   const int nrows = ADJ ? a.C : a.R;
   a.ntiles = (nrows + S::RT - 1) / S::RT;
   const long long ncta = a.tiles ? a.ntiles_list : (long long)a.nblk * a.ntiles;
-  if (ncta == 0) return;
+  if (ncta == 0) return true;
   dim3 grid((unsigned)ncta, (unsigned)((a.b + S::BT - 1) / S::BT));
-  k_stage_mm_vt<ADJ, TX, TB, TR, NT><<<grid, NT, S::SMEM, s>>>(a);
+  k_stage_mm_vt<ADJ, TX, TB, TR, NT, CK><<<grid, NT, S::SMEM, s>>>(a);
+  return true;
 }
-template <typename V, bool ADJ, int TX, int TB, int TR, int NT>
+template <typename V, bool ADJ, int TX, int TB, int TR, int NT, int CK = 32>
 bool launch_vt_if(const StageArgs<V>& a, cudaStream_t s) {
   if constexpr (std::is_same<V, float2>::value) {
-    launch_vt<ADJ, TX, TB, TR, NT>(a, s);
-    return true;
+    return launch_vt<ADJ, TX, TB, TR, NT, CK>(a, s);
   } else {
     return false;
   }
@@ -592,7 +598,8 @@ bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
 // 1..7: tile shapes <TX, TB, TR> of the tiled kernel (256 threads, 64-row tiles, TX x TB
 // right-hand sides per CTA): 1 <8,1,2>, 2 <16,1,4>, 3 <16,2,4>, 4 <8,2,2>, 5 <8,4,2>,
 // 6 <32,1,8>, 7 <16,4,4>; 8: k_stage_vec (b <= 4); complex64 only, contiguous per-thread tiles
-// (k_stage_mm_vt): 9 <16,2,8> with 128 threads, 10 <16,2,4> with 256 threads.  Shapes 2..7, 9, 10
+// (k_stage_mm_vt): 9 <16,2,8> with 128 threads, 10 <16,2,4> with 256 threads, 11 <8,4,8> with 128
+// threads on 128-row tiles (32 accumulators per thread, 16-column chunks).  Shapes 2..7, 9..11
 // need the pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the
 // plain tiled kernel.
 // the TMA-fed persistent tensor-core kernel (k_stage_tma): 30 units of as many row tiles as tensor
@@ -609,9 +616,9 @@ inline bool is_tma_variant(int v) { return v >= kTmaVariant && v <= kTmaShallowV
 constexpr int kFp32CoresVariant = 40;
 inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : (b <= 32 ? 3 : 4))); }
 // candidates per bucket, the built-in choice first
-constexpr int kNCand = 6;
-constexpr int kCand[5][kNCand] = {{8, 1, 0, 0, 0, 0}, {1, 2, 0, 0, 0, 0}, {2, 4, 3, 0, 0, 0},
-                                  {3, 5, 6, 9, 10, 0}, {3, 5, 6, 7, 9, 10}};
+constexpr int kNCand = 7;
+constexpr int kCand[5][kNCand] = {{8, 1, 0, 0, 0, 0, 0}, {1, 2, 0, 0, 0, 0, 0}, {2, 4, 3, 0, 0, 0, 0},
+                                  {3, 5, 6, 9, 10, 11, 0}, {3, 5, 6, 7, 9, 10, 11}};
 
 // launch with variant `var`; false when it does not apply to this launch
 template <typename V, bool ADJ>
@@ -631,6 +638,7 @@ bool launch_variant(const StageArgs<V>& a, cudaStream_t s, int var) {
     case 8: return a.b <= kVecMaxRhs && launch_vec<V, ADJ>(a, s);
     case 9: return pipe && launch_vt_if<V, ADJ, 16, 2, 8, 128>(a, s);
     case 10: return pipe && launch_vt_if<V, ADJ, 16, 2, 4, 256>(a, s);
+    case 11: return pipe && launch_vt_if<V, ADJ, 8, 4, 8, 128, 16>(a, s);
     default: return false;
   }
 }
@@ -880,6 +888,8 @@ StageArgs<V> stage_args(const Stage& st, bool adj, const V* x, long long xrs, lo
   a.dims = st.dims;
   a.tiles = adj ? st.tiles_adj : st.tiles_fwd;
   a.ntiles_list = adj ? st.ntiles_adj : st.ntiles_fwd;
+  a.tiles128 = adj ? st.t128_adj : st.t128_fwd;
+  a.ntiles128 = adj ? st.n128_adj : st.n128_fwd;
   return a;
 }
 
@@ -1332,7 +1342,7 @@ extern "C" int fio_set_variant(fio_op op, int b, int precision, int variant) {
     ti = 2 + mode;
   } else {
     ti = precision == FIO_P64 ? 0 : (precision == FIO_PDF ? 2 : 1);
-    if (variant < 0 || variant > 10 || (variant == 8 && b > kVecMaxRhs) || (variant >= 9 && ti != 1))
+    if (variant < 0 || variant > 11 || (variant == 8 && b > kVecMaxRhs) || (variant >= 9 && ti != 1))
       return FIO_EINVAL;
   }
   for (auto& st : op->st) st.var[ti][0][bucket] = st.var[ti][1][bucket] = (int8_t)variant;

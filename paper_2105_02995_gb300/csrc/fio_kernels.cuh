@@ -166,6 +166,8 @@ struct StageArgs {
   const int2* dims;  // per block (valid rows, valid cols), or nullptr: the padded R x C
   const int2* tiles; // per CTA (block, 64-row tile), or nullptr: blockIdx.x = blk * ntiles + tile
   int ntiles_list;   // length of `tiles`
+  const int2* tiles128;  // per CTA (block, 128-row tile): the work list of 128-row tiles
+  int ntiles128;
 };
 
 // block, row tile and valid extent of the CTA; rows/cols are in the direction of the product
@@ -397,20 +399,23 @@ __global__ void __launch_bounds__(256) k_stage_mm_pipe(StageArgs<V> a) {
 // owning rows ty*TR .. ty*TR+TR-1 and right-hand sides tx*TB .. tx*TB+TB-1 of the CTA tile.  The
 // adjoint reads its TR conjugated factor entries of one column (contiguous in the tile) and both
 // directions read their TB vector entries as float4 pairs, halving the shared-memory
-// instructions per FMA; TR = 8 with 128 threads gives 16 accumulators per thread.
-template <bool ADJ, int TX, int TB, int TR, int NT>
+// instructions per FMA; TR = 8 with 128 threads gives 16 accumulators per thread.  With 8 x 4
+// thread tiles (<8,4,8> on 128 threads) a CTA covers 128 rows and 32 right-hand sides: 32
+// accumulators per thread, 128 FMAs per step of the column loop against 10 shared-memory loads
+// (6 in the adjoint), from the list of 128-row tiles, with chunks of 16 columns.
+template <bool ADJ, int TX, int TB, int TR, int NT, int CK_ = 32>
 struct VtShape {
-  static constexpr int TY = NT / TX, RT = TY * TR, BT = TX * TB, CK = 32;
+  static constexpr int TY = NT / TX, RT = TY * TR, BT = TX * TB, CK = CK_;
   static constexpr int MROWS = ADJ ? CK : RT, MCOLS = ADJ ? RT : CK, MLD = MCOLS + 2;
   static constexpr int SMEM = 2 * (MROWS * MLD + CK * BT) * 8;
 };
 
-template <bool ADJ, int TX, int TB, int TR, int NT>
+template <bool ADJ, int TX, int TB, int TR, int NT, int CK_ = 32>
 __global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
-  using S = VtShape<ADJ, TX, TB, TR, NT>;
+  using S = VtShape<ADJ, TX, TB, TR, NT, CK_>;
   constexpr int RT = S::RT, BT = S::BT, CK = S::CK;
   constexpr int MROWS = S::MROWS, MCOLS = S::MCOLS, MLD = S::MLD;
-  static_assert(TB % 2 == 0 && TR % 2 == 0 && RT == 64, "tile shape");
+  static_assert(TB % 2 == 0 && TR % 2 == 0 && (RT == 64 || RT == 128), "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* sM = reinterpret_cast<float2*>(smem_raw);
   float2* sX = sM + 2 * MROWS * MLD;

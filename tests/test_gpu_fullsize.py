@@ -82,6 +82,7 @@ def test_butterfly_at_sampled_outputs(name):
     f = complex_gaussian(N, b, rhs_seed(3))
     u = op.apply_K(dev(f, dt)).cpu().numpy().astype(np.complex128)
     want = fo.K_rows(ofo, rows, f.astype(np.complex64).astype(np.complex128) if dt == torch.complex64 else f)
+    print(f"[{name}] K-dot vs K at sampled rows: {rel(u[rows], want):.3g}")
     assert rel(u[rows], want) < kbound
     # K* x at sampled outputs: (K* x)_j = sum_i conj(K_ij) x_i, one column of K at a time
     x = complex_gaussian(N, b, rhs_seed(3, 1))
@@ -89,6 +90,7 @@ def test_butterfly_at_sampled_outputs(name):
     cols = rows[:16]
     Kc = fo.K_block(ofo, np.arange(N), cols)
     xx = x.astype(np.complex64).astype(np.complex128) if dt == torch.complex64 else x
+    print(f"[{name}] K-dot* vs K* at sampled outputs: {rel(y[cols], Kc.conj().T @ xx):.3g}")
     assert rel(y[cols], Kc.conj().T @ xx) < kbound
 
 
@@ -100,6 +102,7 @@ def test_direct_solve_sampled_residual(name):
     u = complex_gaussian(N, b, rhs_seed(4))
     f = op.apply_inv(dev(u, dt)).cpu().numpy().astype(np.complex128)
     rows = np.sort(np.random.default_rng(5).choice(N, 48, replace=False))
+    print(f"[{name}] direct solve, sampled residual: {rel(fo.K_rows(ofo, rows, f), u[rows]):.3g}")
     assert rel(fo.K_rows(ofo, rows, f), u[rows]) < sbound
 
 

@@ -329,7 +329,7 @@ def test_exact_initial_guess_needs_no_iteration(method):
 # Autotuner: every tile-shape variant sums each output's terms in the same order, so for b >= 5
 # the tuned applies must reproduce the built-in ones bit for bit; for b <= 4 the few-RHS kernel
 # (tree reductions) may be chosen, within the parity tolerances above.
-ALLOWED = {0: {0, 8, 1}, 1: {0, 1, 2}, 2: {0, 2, 3, 4}, 3: {0, 3, 5, 6, 9, 10}, 4: {0, 3, 5, 6, 7, 9, 10}}
+ALLOWED = {0: {0, 8, 1}, 1: {0, 1, 2}, 2: {0, 2, 3, 4}, 3: {0, 3, 5, 6, 9, 10, 11}, 4: {0, 3, 5, 6, 7, 9, 10, 11}}
 
 
 def _bucket(b):
@@ -382,7 +382,7 @@ def test_every_tile_shape_is_bit_identical(name, prec, dt):
     xd = dev(complex_gaussian(ofo.N, b, rhs_seed(0, 700)), dt)
     op.set_variant(b, prec, 0)
     ref = {w: getattr(op, "apply_" + w)(xd, precision=prec).clone() for w in ("K", "Kadj", "inv")}
-    for var in list(range(1, 8)) + ([9, 10] if prec == binding.FIO_P32 else []):
+    for var in list(range(1, 8)) + ([9, 10, 11] if prec == binding.FIO_P32 else []):
         op.set_variant(b, prec, var)
         for w in ("K", "Kadj", "inv"):
             y = getattr(op, "apply_" + w)(xd, precision=prec)
@@ -456,7 +456,8 @@ def test_tensor_core_split_inplace_stages(name, prec, b):
 def test_set_variant_rejects_unknown_variants():
     buf, info, P, op, ofo = get("ex3_32")
     lib = binding.load()
-    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 11) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 12) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 11) == -1   # complex64-only tiles
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 9) == -1    # complex64-only tiles
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 8) == -1    # few-RHS kernel needs b <= 4
     assert lib.fio_set_variant(op.h, 16, binding.FIO_PTF32, 3) == -1  # tensor-core launch: 0, 20-22, 30
