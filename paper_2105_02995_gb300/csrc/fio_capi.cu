@@ -547,7 +547,7 @@ bool launch_vt(StageArgs<float2> a, cudaStream_t s) {
   a.ntiles = (nrows + S::RT - 1) / S::RT;
   const long long ncta = a.tiles ? a.ntiles_list : (long long)a.nblk * a.ntiles;
   if (ncta == 0) return true;
-  dim3 grid((unsigned)ncta, (unsigned)((a.b + S::BT - 1) / S::BT));
+  dim3 grid((unsigned)ncta, (unsigned)((a.b + S::BT - 1) / S::BT), (unsigned)a.ksplit);
   k_stage_mm_vt<ADJ, TX, TB, TR, NT, CK><<<grid, NT, S::SMEM, s>>>(a);
   return true;
 }
@@ -599,7 +599,8 @@ bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
 // right-hand sides per CTA): 1 <8,1,2>, 2 <16,1,4>, 3 <16,2,4>, 4 <8,2,2>, 5 <8,4,2>,
 // 6 <32,1,8>, 7 <16,4,4>; 8: k_stage_vec (b <= 4); complex64 only, contiguous per-thread tiles
 // (k_stage_mm_vt): 9 <16,2,8> with 128 threads, 10 <16,2,4> with 256 threads, 11 <8,4,8> with 128
-// threads on 128-row tiles (32 accumulators per thread, 16-column chunks).  Shapes 2..7, 9..11
+// threads on 128-row tiles (32 accumulators per thread, 16-column chunks), 12 the same with the
+// in-place stages split over their columns (partial sums reduced in a fixed order).  Shapes 2..7, 9..11
 // need the pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the
 // plain tiled kernel.
 // the TMA-fed persistent tensor-core kernel (k_stage_tma): 30 units of as many row tiles as tensor
@@ -616,9 +617,9 @@ inline bool is_tma_variant(int v) { return v >= kTmaVariant && v <= kTmaShallowV
 constexpr int kFp32CoresVariant = 40;
 inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : (b <= 32 ? 3 : 4))); }
 // candidates per bucket, the built-in choice first
-constexpr int kNCand = 7;
-constexpr int kCand[5][kNCand] = {{8, 1, 0, 0, 0, 0, 0}, {1, 2, 0, 0, 0, 0, 0}, {2, 4, 3, 0, 0, 0, 0},
-                                  {3, 5, 6, 9, 10, 11, 0}, {3, 5, 6, 7, 9, 10, 11}};
+constexpr int kNCand = 8;
+constexpr int kCand[5][kNCand] = {{8, 1, 0, 0, 0, 0, 0, 0}, {1, 2, 0, 0, 0, 0, 0, 0}, {2, 4, 3, 0, 0, 0, 0, 0},
+                                  {3, 5, 6, 9, 10, 11, 12}, {3, 5, 6, 7, 9, 10, 11, 12}};
 
 // launch with variant `var`; false when it does not apply to this launch
 template <typename V, bool ADJ>
@@ -638,9 +639,21 @@ bool launch_variant(const StageArgs<V>& a, cudaStream_t s, int var) {
     case 8: return a.b <= kVecMaxRhs && launch_vec<V, ADJ>(a, s);
     case 9: return pipe && launch_vt_if<V, ADJ, 16, 2, 8, 128>(a, s);
     case 10: return pipe && launch_vt_if<V, ADJ, 16, 2, 4, 256>(a, s);
-    case 11: return pipe && launch_vt_if<V, ADJ, 8, 4, 8, 128, 16>(a, s);
+    case 11:
+    case 12: return pipe && launch_vt_if<V, ADJ, 8, 4, 8, 128, 16>(a, s);
     default: return false;
   }
+}
+
+// whether CUDA-core variant `var` runs this launch as itself (else launch_variant declines it)
+template <typename V>
+bool variant_applies(const StageArgs<V>& a, int var) {
+  const bool pipe = pipe_ok(a);
+  if (var == 1) return true;
+  if (var >= 2 && var <= 7) return pipe;
+  if (var == 8) return a.b <= kVecMaxRhs;
+  if (var >= 9 && var <= 12) return pipe && std::is_same<V, float2>::value && (var < 11 || a.tiles128);
+  return false;
 }
 
 // var: the tuned variant of this launch (0 = none): else the built-in choice by b
@@ -919,11 +932,39 @@ template <typename V>
 bool inplace_split(const Stage&, bool, V*, V*, long long, int, cudaStream_t) {
   return false;
 }
+constexpr int kFp32SplitVariant = 12;
+
+// the FP32 CUDA-core split (variant 12): 128-row tiles of 8 x 4 thread tiles, about two CTAs per
+// SM slot, at least four 16-column chunks per slice
+bool inplace_split_fp32(const Stage& st, bool adj, float2* W, float2* P, long long pcap, int b, cudaStream_t s) {
+  StageArgs<float2> a = stage_args<float2>(st, adj, W, b, 1, W, b, 1, b);
+  if (!pipe_ok(a) || !a.tiles128 || a.ntiles128 <= 0) return false;
+  const long long prow = (long long)st.nblk * (adj ? st.C : st.R);
+  if (prow <= 0 || prow > pcap) return false;
+  const int dir = adj ? 1 : 0;
+  const long long ctas = (long long)a.ntiles128 * ((b + 31) / 32);
+  const int nch = (st.maxcols[dir] + 15) / 16;
+  long long ks = (8LL * num_sms() + ctas - 1) / ctas;
+  ks = std::min<long long>(ks, std::max(1, nch / 4));
+  ks = std::min<long long>(ks, pcap / prow);
+  a.ksplit = (int)std::max<long long>(1, std::min<long long>(ks, 64));
+  a.part = P;
+  a.prow = prow;
+  const bool ok = adj ? launch_vt<true, 8, 4, 8, 128, 16>(a, s) : launch_vt<false, 8, 4, 8, 128, 16>(a, s);
+  if (!ok) return false;
+  const long long tot = prow * b;
+  k_partial_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, a.ksplit, prow, b, st.out, W);
+  return true;
+}
+
 template <>
 bool inplace_split<float2>(const Stage& st, bool adj, float2* W, float2* P, long long pcap, int b, cudaStream_t s) {
-  if (!P || !use_tc<float2>(st, b, adj)) return false;
-  if (st.var[2 + g_tc_mode][adj ? 1 : 0][rhs_bucket(b)] != kTmaSplitVariant) return false;
-  const int dir = adj ? 1 : 0;
+  if (!P) return false;
+  const int bk = rhs_bucket(b), dir = adj ? 1 : 0;
+  const bool tc = use_tc<float2>(st, b, adj);
+  if (!tc || st.var[2 + g_tc_mode][dir][bk] == kFp32CoresVariant)
+    return st.var[1][dir][bk] == kFp32SplitVariant && inplace_split_fp32(st, adj, W, P, pcap, b, s);
+  if (st.var[2 + g_tc_mode][dir][bk] != kTmaSplitVariant) return false;
   const long long prow = (long long)st.nblk * (adj ? st.C : st.R);
   const int units = st.nunits[dir][0];
   if (prow <= 0 || units <= 0 || prow > pcap) return false;
@@ -1279,11 +1320,12 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
           const int var = tc ? kTcCand[k] : kCand[bucket][k];
           if (var <= 0 && !tc) break;
           float t;
-          if (tc && st.kind == 1) {
+          if (st.kind == 1) {
             // in-place stages: the whole stage (compute and copy-back, or split compute and
             // reduction), so that the split variant is weighed with its reduction
             t = time_launch(
                 [&] {
+                  if (!tc && !variant_applies<V>(a, var)) return false;
                   st.var[ti][dir][bucket] = (int8_t)var;
                   inplace_stage<V>(st, adj, X, Y, b, s, (V*)bufs[2], op->max_len);
                   return true;
@@ -1342,7 +1384,7 @@ extern "C" int fio_set_variant(fio_op op, int b, int precision, int variant) {
     ti = 2 + mode;
   } else {
     ti = precision == FIO_P64 ? 0 : (precision == FIO_PDF ? 2 : 1);
-    if (variant < 0 || variant > 11 || (variant == 8 && b > kVecMaxRhs) || (variant >= 9 && ti != 1))
+    if (variant < 0 || variant > 12 || (variant == 8 && b > kVecMaxRhs) || (variant >= 9 && ti != 1))
       return FIO_EINVAL;
   }
   for (auto& st : op->st) st.var[ti][0][bucket] = st.var[ti][1][bucket] = (int8_t)variant;

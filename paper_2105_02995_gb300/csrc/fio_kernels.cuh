@@ -168,6 +168,12 @@ struct StageArgs {
   int ntiles_list;   // length of `tiles`
   const int2* tiles128;  // per CTA (block, 128-row tile): the work list of 128-row tiles
   int ntiles128;
+  // split over the block's columns (k_stage_mm_vt, in-place stages): blockIdx.z is the slice;
+  // slice ks of row r of block blk goes to part[(ks * prow + blk * rows + r) * b + j], rows the
+  // block's rows in the product's direction (summed by k_partial_reduce); part == nullptr: none
+  int ksplit = 1;
+  V* part = nullptr;
+  long long prow = 0;
 };
 
 // block, row tile and valid extent of the CTA; rows/cols are in the direction of the product
@@ -465,11 +471,15 @@ __global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
 #pragma unroll
     for (int k = 0; k < TB; ++k) acc[i][k] = make_float2(0.f, 0.f);
 
-  const int nchunks = (ncols + CK - 1) / CK;
-  load(0, 0);
+  // the slice of the block's column chunks this CTA sums (all of them unless split)
+  const int nch = (ncols + CK - 1) / CK;
+  const int cps = (nch + a.ksplit - 1) / a.ksplit;
+  const int kb = min(nch, (int)blockIdx.z * cps);
+  const int nchunks = min(nch, kb + cps) - kb;
+  if (nchunks > 0) load(0, kb * CK);
   for (int k = 0; k < nchunks; ++k) {
     if (k + 1 < nchunks) {
-      load((k + 1) & 1, (k + 1) * CK);
+      load((k + 1) & 1, (kb + k + 1) * CK);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -510,10 +520,13 @@ __global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
     if (r >= nrows) continue;
     const int idx = rowidx[r];
     if (idx < 0) continue;
+    float2* dst = a.part ? a.part + ((long long)blockIdx.z * a.prow + (long long)blk * (ADJ ? a.C : a.R) + r) * a.b
+                         : a.y + (long long)idx * a.yrs;
+    const long long cs = a.part ? 1 : a.ycs;
 #pragma unroll
     for (int q = 0; q < TB; ++q) {
       const int j = j0 + tx * TB + q;
-      if (j < a.b) a.y[(long long)idx * a.yrs + (long long)j * a.ycs] = acc[i][q];
+      if (j < a.b) dst[(long long)j * cs] = acc[i][q];
     }
   }
 }
