@@ -194,28 +194,36 @@ int fio_solve(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
  * and bucket use the choice; untuned ones keep the built-in choice by b.  Variants: 1..7 tile
  * shapes <TX,TB,TR> of the tiled stage kernel (1 <8,1,2>, 2 <16,1,4>, 3 <16,2,4>, 4 <8,2,2>,
  * 5 <8,4,2>, 6 <32,1,8>, 7 <16,4,4>: TX x TB right-hand sides and 64 rows per 256-thread CTA),
- * 8 the few-right-hand-side kernel (b <= 4), 9 / 10 complex64 tiles with contiguous per-thread
- * rows and right-hand sides (<16,2,8> on 128 threads, <16,2,4> on 256); with a tensor-core
+ * 8 the few-right-hand-side kernel (b <= 4), 9 / 10 / 11 complex64 tiles with contiguous
+ * per-thread rows and right-hand sides (<16,2,8> on 128 threads, <16,2,4> on 256, <8,4,8> on 128
+ * threads and 128-row tiles), 12 variant 11 with every in-place stage (HIF nodes, root) split
+ * over its columns into slices summed by a fixed-order reduction, 13 (FP64 and FP32, b >= 5) one
+ * warp per block for stages whose padded blocks are at most 32 x 32 (the leaf stages), 14 / 15 /
+ * 16 (FP64 and double-float) the tiles of 3 / 6 / 2 with three real products per complex
+ * product on the butterfly stages (Gauss's 3M form: the imaginary part's rounding error up to a
+ * few times the four-product one; the in-place HIF stages keep four products); with a tensor-core
  * precision and b >= 8: 0 the single-buffer tcgen05 kernel, 20 / 21 / 22 its warp-specialised
  * ring variant with 2 / 3 / 4 chunk stages, 30 the persistent tcgen05 kernel whose factor tiles
  * arrive by TMA (work units of as many 128-row tiles as tensor memory holds, deepest ring), 31
  * the same with every in-place stage (HIF nodes, root) split over its columns into slices summed
  * by a fixed-order reduction (enough work units for the few large blocks of the top levels), 32
  * the TMA kernel with units sized for about eight per SM, 33 the TMA kernel with a six-slot
- * ring; 0 also for empty stages.  Stages whose rows are not 16-byte aligned (an odd width in a
- * hand-packed buffer) and odd b keep variant 0 or the FP32 CUDA cores.
- * Every variant sums each output's terms in the same order, except 8 (tree reductions) and 31
- * (the in-place stages' slices), so results for b >= 5 do not depend on the choice otherwise.  choices (may be NULL when cap == 0) receives
+ * ring, 40 the stage launch on the FP32 CUDA cores with FP32's tuned tile; 0 also for empty
+ * stages.  Stages whose rows are not 16-byte aligned (an odd width in a hand-packed buffer) and
+ * odd b keep variant 0 or the FP32 CUDA cores.
+ * Every variant sums each output's terms in the same order, except 8 (tree reductions), 12 and
+ * 31 (the in-place stages' slices) and 14..16 (three products), so results for b >= 5 do not
+ * depend on the choice otherwise.  choices (may be NULL when cap == 0) receives
  * the variant per stage launch in stage order, forward before adjoint (the root: forward
  * only); *nchoices (may be NULL) their number.  Synchronises `stream`; must not run
  * concurrently with other calls on the operator. */
 int fio_autotune(fio_op op, int b, int precision, void* stream, int* choices, int cap, int* nchoices);
 
 /* Pin the kernel variant of every stage launch of (precision, the bucket of b) to `variant`
- * (0 = the built-in choice): 1..10 as for fio_autotune on the CUDA cores (8 only for b <= 4, 9
- * and 10 only for FIO_P32); with a tensor-core precision and b >= 8, 0 (single-buffer kernel),
- * 20, 21, 22 (the warp-specialised ring kernel with 2, 3, 4 chunk stages) or 30..33 (the
- * TMA-fed persistent kernel, as for fio_autotune); a variant that does not apply to a stage
+ * (0 = the built-in choice): 1..16 as for fio_autotune on the CUDA cores (8 only for b <= 4,
+ * 9..12 only for FIO_P32, 13 not for FIO_PDF, 14..16 only for FIO_P64 and FIO_PDF); with a tensor-core precision and b >= 8, 0 (single-buffer kernel),
+ * 20, 21, 22 (the warp-specialised ring kernel with 2, 3, 4 chunk stages), 30..33 (the
+ * TMA-fed persistent kernel, as for fio_autotune) or 40 (FP32 CUDA cores); a variant that does not apply to a stage
  * (shared memory, alignment, odd b) falls back to 0.  Host-only; FIO_EINVAL for a variant that
  * does not exist for the pair. */
 int fio_set_variant(fio_op op, int b, int precision, int variant);

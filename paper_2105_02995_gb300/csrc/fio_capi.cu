@@ -530,6 +530,25 @@ void launch_pipe(StageArgs<V> a, cudaStream_t s) {
   dim3 grid((unsigned)ncta, (unsigned)((a.b + S::BT - 1) / S::BT));
   k_stage_mm_pipe<V, ADJ, TX, TB, TR, CK><<<grid, 256, S::SMEM, s>>>(a);
 }
+// the same tiles with three real products per complex product (FP64 and double-float only)
+template <typename V, bool ADJ, int TX, int TB, int TR>
+bool launch_pipe3(StageArgs<V> a, cudaStream_t s) {
+  if constexpr (std::is_same<V, double2>::value || std::is_same<V, dfc>::value) {
+    constexpr int CK = ChunkK<V>::v;
+    using S = PipeShape<V, ADJ, TX, TB, TR, CK>;
+    constexpr int smem = S::smem(true);
+    if (!smem_opt_in((const void*)k_stage_mm_pipe<V, ADJ, TX, TB, TR, CK, true>, smem)) return false;
+    const int nrows = ADJ ? a.C : a.R;
+    a.ntiles = (nrows + S::RT - 1) / S::RT;
+    const long long ncta = a.tiles ? a.ntiles_list : (long long)a.nblk * a.ntiles;
+    if (ncta == 0) return true;
+    dim3 grid((unsigned)ncta, (unsigned)((a.b + S::BT - 1) / S::BT));
+    k_stage_mm_pipe<V, ADJ, TX, TB, TR, CK, true><<<grid, 256, smem, s>>>(a);
+    return true;
+  } else {
+    return false;
+  }
+}
 
 // complex64 tiles with contiguous per-thread rows and right-hand sides (k_stage_mm_vt); 64- or
 // 128-row tiles (the latter from the stage's list of 128-row tiles)
@@ -555,6 +574,27 @@ template <typename V, bool ADJ, int TX, int TB, int TR, int NT, int CK = 32>
 bool launch_vt_if(const StageArgs<V>& a, cudaStream_t s) {
   if constexpr (std::is_same<V, float2>::value) {
     return launch_vt<ADJ, TX, TB, TR, NT, CK>(a, s);
+  } else {
+    return false;
+  }
+}
+
+// small blocks (k_stage_small, FP64 and FP32): a warp per block, 32 right-hand sides per CTA row
+template <typename V>
+bool small_ok(const StageArgs<V>& a) {
+  return (std::is_same<V, float2>::value || std::is_same<V, double2>::value) && a.R <= kSmallMaxDim &&
+         a.C <= kSmallMaxDim && a.R > 0 && a.C > 0;
+}
+template <typename V, bool ADJ>
+bool launch_small(const StageArgs<V>& a, cudaStream_t s) {
+  if constexpr (std::is_same<V, float2>::value || std::is_same<V, double2>::value) {
+    if (!small_ok(a)) return false;
+    const int smem = kSmallWarps * (a.R * a.C + 32 * (ADJ ? a.R : a.C)) * (int)sizeof(V);
+    if (!smem_opt_in((const void*)k_stage_small<V, ADJ>, smem)) return false;
+    if (a.nblk == 0) return true;
+    dim3 grid((unsigned)((a.nblk + kSmallWarps - 1) / kSmallWarps), (unsigned)((a.b + 31) / 32));
+    k_stage_small<V, ADJ><<<grid, 32 * kSmallWarps, smem, s>>>(a);
+    return true;
   } else {
     return false;
   }
@@ -600,9 +640,13 @@ bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
 // 6 <32,1,8>, 7 <16,4,4>; 8: k_stage_vec (b <= 4); complex64 only, contiguous per-thread tiles
 // (k_stage_mm_vt): 9 <16,2,8> with 128 threads, 10 <16,2,4> with 256 threads, 11 <8,4,8> with 128
 // threads on 128-row tiles (32 accumulators per thread, 16-column chunks), 12 the same with the
-// in-place stages split over their columns (partial sums reduced in a fixed order).  Shapes 2..7, 9..11
-// need the pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the
-// plain tiled kernel.
+// in-place stages split over their columns (partial sums reduced in a fixed order); 13
+// k_stage_small (a warp per block, FP64 and FP32, padded blocks up to 32 x 32); 14, 15, 16 the
+// FP64 and double-float tiles of 3, 6, 2 with three real products per complex product
+// (k_stage_mm_pipe's G3) on the butterfly stages (the in-place stages, where the HIF's
+// conditioning amplifies rounding, keep four products).  Shapes 2..7, 9..12, 14..16 need the
+// pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the plain
+// tiled kernel.
 // the TMA-fed persistent tensor-core kernel (k_stage_tma): 30 units of as many row tiles as tensor
 // memory holds and the deepest A ring; 31 the same with in-place stages split over K; 32 units
 // sized for about eight per SM; 33 an A ring of at most six slots (split TF32: a six-slot tail
@@ -617,9 +661,15 @@ inline bool is_tma_variant(int v) { return v >= kTmaVariant && v <= kTmaShallowV
 constexpr int kFp32CoresVariant = 40;
 inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : (b <= 32 ? 3 : 4))); }
 // candidates per bucket, the built-in choice first
-constexpr int kNCand = 8;
-constexpr int kCand[5][kNCand] = {{8, 1, 0, 0, 0, 0, 0, 0}, {1, 2, 0, 0, 0, 0, 0, 0}, {2, 4, 3, 0, 0, 0, 0, 0},
-                                  {3, 5, 6, 9, 10, 11, 12}, {3, 5, 6, 7, 9, 10, 11, 12}};
+constexpr int kSmallVariant = 13;
+constexpr int kMaxCudaCoreVariant = 16;
+inline bool is_3m_variant(int v) { return v >= 14 && v <= 16; }
+// the four-product variant a three-product one stands for on the in-place stages
+inline int four_product_of(int v) { return v == 14 ? 3 : v == 15 ? 6 : v == 16 ? 2 : v; }
+constexpr int kNCand = 11;
+constexpr int kCand[5][kNCand] = {{8, 1}, {1, 2, 13, 16}, {2, 4, 3, 13, 14, 16},
+                                  {3, 5, 6, 9, 10, 11, 12, 13, 14, 15},
+                                  {3, 5, 6, 7, 9, 10, 11, 12, 13, 14, 15}};
 
 // launch with variant `var`; false when it does not apply to this launch
 template <typename V, bool ADJ>
@@ -641,6 +691,10 @@ bool launch_variant(const StageArgs<V>& a, cudaStream_t s, int var) {
     case 10: return pipe && launch_vt_if<V, ADJ, 16, 2, 4, 256>(a, s);
     case 11:
     case 12: return pipe && launch_vt_if<V, ADJ, 8, 4, 8, 128, 16>(a, s);
+    case kSmallVariant: return launch_small<V, ADJ>(a, s);
+    case 14: return pipe && launch_pipe3<V, ADJ, 16, 2, 4>(a, s);
+    case 15: return pipe && launch_pipe3<V, ADJ, 32, 1, 8>(a, s);
+    case 16: return pipe && launch_pipe3<V, ADJ, 16, 1, 4>(a, s);
     default: return false;
   }
 }
@@ -653,6 +707,8 @@ bool variant_applies(const StageArgs<V>& a, int var) {
   if (var >= 2 && var <= 7) return pipe;
   if (var == 8) return a.b <= kVecMaxRhs;
   if (var >= 9 && var <= 12) return pipe && std::is_same<V, float2>::value && (var < 11 || a.tiles128);
+  if (var == kSmallVariant) return small_ok(a);
+  if (is_3m_variant(var)) return pipe && !std::is_same<V, float2>::value;
   return false;
 }
 
@@ -919,7 +975,8 @@ void launch_stage(const Stage& st, bool adj, const V* x, long long xrs, long lon
     }
   }
   const StageArgs<V> a = stage_args<V>(st, adj, x, xrs, xcs, y, yrs, ycs, b);
-  const int var = st.var[type_index<V>()][adj ? 1 : 0][rhs_bucket(b)];
+  int var = st.var[type_index<V>()][adj ? 1 : 0][rhs_bucket(b)];
+  if (st.kind == 1) var = four_product_of(var);  // in-place stages keep four products
   if (adj) launch_stage_dir<V, true>(a, s, var);
   else launch_stage_dir<V, false>(a, s, var);
 }
@@ -1325,7 +1382,7 @@ int tune_type(fio_op op, int b, cudaStream_t s, int* choices, int cap, int* nch)
             // reduction), so that the split variant is weighed with its reduction
             t = time_launch(
                 [&] {
-                  if (!tc && !variant_applies<V>(a, var)) return false;
+                  if (!tc && (!variant_applies<V>(a, var) || is_3m_variant(var))) return false;
                   st.var[ti][dir][bucket] = (int8_t)var;
                   inplace_stage<V>(st, adj, X, Y, b, s, (V*)bufs[2], op->max_len);
                   return true;
@@ -1384,7 +1441,9 @@ extern "C" int fio_set_variant(fio_op op, int b, int precision, int variant) {
     ti = 2 + mode;
   } else {
     ti = precision == FIO_P64 ? 0 : (precision == FIO_PDF ? 2 : 1);
-    if (variant < 0 || variant > 12 || (variant == 8 && b > kVecMaxRhs) || (variant >= 9 && ti != 1))
+    if (variant < 0 || variant > kMaxCudaCoreVariant || (variant == 8 && b > kVecMaxRhs) ||
+        (variant >= 9 && variant < kSmallVariant && ti != 1) || (variant == kSmallVariant && ti == 2) ||
+        (is_3m_variant(variant) && ti == 1))
       return FIO_EINVAL;
   }
   for (auto& st : op->st) st.var[ti][0][bucket] = st.var[ti][1][bucket] = (int8_t)variant;

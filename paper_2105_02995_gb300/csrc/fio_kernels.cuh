@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace fio {
 
 __device__ __forceinline__ double2 cmac(double2 acc, double2 a, double2 b) {
@@ -291,20 +293,84 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// Three real products per complex product (Gauss's form of the 3M method; error analysis in
+// Higham, "Stability of a method for multiplying complex matrices with three real matrix
+// multiplications", 1992) for the FP64 and double-float stage products, where every multiply is
+// costly (GB300's FP64 pipes; 12 FP32 operations per double-float product).  With m = a + ib and
+// x = c + id:
+//     p1 += a c,  p2 += b d,  p3 += (a +- b)(c + d);  forward (p1 - p2) + i ((p3 - p1) - p2),
+//                                                     adjoint (p1 + p2) + i ((p3 - p1) + p2)
+// The real part is the four-product method's two sums; the imaginary part is a difference of
+// three sums, whose rounding errors scale with (|a| + |b|)(|c| + |d|) instead of |a||d| + |b||c|
+// (at most a few times larger).  The sums a +- b and c + d are formed once per chunk in shared
+// memory (a real value of the arithmetic: a double, or a double-float pair added with TwoSum).
+// G3Ops<V> is the arithmetic.
+template <typename V> struct G3Ops;
+template <> struct G3Ops<double2> {
+  using S = double;  // a sum a +- b or c + d
+  using A = double;  // one of the three running sums
+  static __device__ __forceinline__ A zero() { return 0.0; }
+  static __device__ __forceinline__ S sum_m(double2 m, bool adj) { return adj ? __dsub_rn(m.x, m.y) : __dadd_rn(m.x, m.y); }
+  static __device__ __forceinline__ S sum_x(double2 x) { return __dadd_rn(x.x, x.y); }
+  static __device__ __forceinline__ void step(A& p1, A& p2, A& p3, double2 m, S sm, double2 x, S tx) {
+    p1 = fma(m.x, x.x, p1);
+    p2 = fma(m.y, x.y, p2);
+    p3 = fma(sm, tx, p3);
+  }
+  static __device__ __forceinline__ double2 fin(A p1, A p2, A p3, bool adj) {
+    return adj ? make_double2(__dadd_rn(p1, p2), __dadd_rn(__dsub_rn(p3, p1), p2))
+               : make_double2(__dsub_rn(p1, p2), __dsub_rn(__dsub_rn(p3, p1), p2));
+  }
+};
+// double-float a + b (Knuth's TwoSum of the leading parts, the trailing parts and the error
+// added, renormalised by Fast2Sum)
+__device__ __forceinline__ float2 df_add(float ah, float al, float bh, float bl) {
+  const float s = __fadd_rn(ah, bh);
+  const float z = __fsub_rn(s, ah);
+  const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, z)), __fsub_rn(bh, z));
+  const float c = __fadd_rn(e, __fadd_rn(al, bl));
+  const float hi = __fadd_rn(s, c);
+  return make_float2(hi, __fsub_rn(c, __fsub_rn(hi, s)));
+}
+template <> struct G3Ops<dfc> {
+  using S = float2;  // double-float (hi, lo)
+  using A = float2;  // Dot2 accumulator (s, c)
+  static __device__ __forceinline__ A zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ S sum_m(dfc m, bool adj) {
+    return adj ? df_add(m.rh, m.rl, -m.ih, -m.il) : df_add(m.rh, m.rl, m.ih, m.il);
+  }
+  static __device__ __forceinline__ S sum_x(dfc x) { return df_add(x.rh, x.rl, x.ih, x.il); }
+  static __device__ __forceinline__ void step(A& p1, A& p2, A& p3, dfc m, S sm, dfc x, S tx) {
+    dot2_step(p1.x, p1.y, m.rh, m.rl, x.rh, x.rl);
+    dot2_step(p2.x, p2.y, m.ih, m.il, x.ih, x.il);
+    dot2_step(p3.x, p3.y, sm.x, sm.y, tx.x, tx.y);
+  }
+  // the accumulator form (re s, im s, re c, im c) that cfin renormalises
+  static __device__ __forceinline__ dfc fin(A p1, A p2, A p3, bool adj) {
+    float rs = p1.x, rc = p1.y, is = p3.x, ic = p3.y;
+    df_acc_add(rs, rc, adj ? p2.x : -p2.x, adj ? p2.y : -p2.y);
+    df_acc_add(is, ic, -p1.x, -p1.y);
+    df_acc_add(is, ic, adj ? p2.x : -p2.x, adj ? p2.y : -p2.y);
+    return dfc{rs, is, rc, ic};
+  }
+};
+
 // Same contract as k_stage_mm, for the internal row-major vectors (xrs = b, xcs = 1) with every
 // copied row 16-byte aligned (C * sizeof(V) and b * sizeof(V) multiples of 16).  Chunk k+1 of the
 // block's columns (its M tile and its gathered x rows) is in flight while chunk k is multiplied;
 // out-of-range and padding copies are zero-filled (source size 0).  Dynamic shared memory:
-// 2 * (MROWS * MLD + CK * BT) * sizeof(V).
+// 2 * (MROWS * MLD + CK * BT) * sizeof(V), and with G3 (FP64 and double-float only) the two
+// planes of sums beside the tiles, 8 bytes per entry.
 template <typename V, bool ADJ, int TX, int TB, int TR, int CK>
 struct PipeShape {
   static constexpr int TY = 256 / TX, RT = TY * TR, BT = TX * TB;
   static constexpr int VPC = 16 / (int)sizeof(V);  // complex values per 16-byte copy
   static constexpr int MROWS = ADJ ? CK : RT, MCOLS = ADJ ? RT : CK, MLD = MCOLS + VPC;
   static constexpr int SMEM = 2 * (MROWS * MLD + CK * BT) * (int)sizeof(V);
+  static constexpr int smem(bool g3) { return SMEM + (g3 ? 2 * (MROWS * MLD + CK * BT) * 8 : 0); }
 };
 
-template <typename V, bool ADJ, int TX, int TB, int TR, int CK>
+template <typename V, bool ADJ, int TX, int TB, int TR, int CK, bool G3 = false>
 __global__ void __launch_bounds__(256) k_stage_mm_pipe(StageArgs<V> a) {
   using S = PipeShape<V, ADJ, TX, TB, TR, CK>;
   constexpr int TY = S::TY, RT = S::RT, BT = S::BT, VPC = S::VPC;
@@ -358,6 +424,20 @@ __global__ void __launch_bounds__(256) k_stage_mm_pipe(StageArgs<V> a) {
   for (int i = 0; i < TR; ++i)
 #pragma unroll
     for (int k = 0; k < TB; ++k) acc[i][k] = czero<V>();
+  // G3: the three running sums of every output and the planes of sums (types of G3Ops<V>)
+  using Ops = G3Ops<typename std::conditional<G3, V, double2>::type>;
+  using GS = typename Ops::S;
+  using GA = typename Ops::A;
+  constexpr int GR = G3 ? TR : 1, GB = G3 ? TB : 1;
+  GA p1[GR][GB], p2[GR][GB], p3[GR][GB];
+  GS* sS = reinterpret_cast<GS*>(sX + 2 * CK * BT);  // [2][MROWS][MLD]
+  GS* sT = sS + 2 * MROWS * MLD;                      // [2][CK][BT]
+  if constexpr (G3) {
+#pragma unroll
+    for (int i = 0; i < TR; ++i)
+#pragma unroll
+      for (int k = 0; k < TB; ++k) p1[i][k] = p2[i][k] = p3[i][k] = Ops::zero();
+  }
 
   const int nchunks = (ncols + CK - 1) / CK;
   load(0, 0);
@@ -371,19 +451,59 @@ __global__ void __launch_bounds__(256) k_stage_mm_pipe(StageArgs<V> a) {
     __syncthreads();
     const V* tM = sM + (k & 1) * MROWS * MLD;
     const V* tX = sX + (k & 1) * CK * BT;
+    if constexpr (G3) {
+      // the chunk's sums, once: a +- b of every factor entry, c + d of every x entry
+      GS* wS = sS + (k & 1) * MROWS * MLD;
+      GS* wT = sT + (k & 1) * CK * BT;
+      for (int e = tid; e < MROWS * MCOLS; e += 256) {
+        const int mr = e / MCOLS, mc = e - mr * MCOLS;
+        wS[mr * MLD + mc] = Ops::sum_m(tM[mr * MLD + mc], ADJ);
+      }
+      for (int e = tid; e < CK * BT; e += 256) wT[e] = Ops::sum_x(tX[e]);
+      __syncthreads();
+      const GS* tS = wS;
+      const GS* tT = wT;
+#pragma unroll 4
+      for (int cc = 0; cc < CK; ++cc) {
+        V m[TR], xv[TB];
+        GS sm[TR], tx3[TB];
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+          const int o = ADJ ? cc * MLD + ty + TY * i : (ty + TY * i) * MLD + cc;
+          m[i] = tM[o];
+          sm[i] = tS[o];
+        }
+#pragma unroll
+        for (int q = 0; q < TB; ++q) {
+          xv[q] = tX[cc * BT + tx + TX * q];
+          tx3[q] = tT[cc * BT + tx + TX * q];
+        }
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+          for (int q = 0; q < TB; ++q) Ops::step(p1[i][q], p2[i][q], p3[i][q], m[i], sm[i], xv[q], tx3[q]);
+      }
+    } else {
 #pragma unroll 8
-    for (int cc = 0; cc < CK; ++cc) {
-      V m[TR], xv[TB];
+      for (int cc = 0; cc < CK; ++cc) {
+        V m[TR], xv[TB];
 #pragma unroll
-      for (int i = 0; i < TR; ++i) m[i] = ADJ ? tM[cc * MLD + ty + TY * i] : tM[(ty + TY * i) * MLD + cc];
+        for (int i = 0; i < TR; ++i) m[i] = ADJ ? tM[cc * MLD + ty + TY * i] : tM[(ty + TY * i) * MLD + cc];
 #pragma unroll
-      for (int q = 0; q < TB; ++q) xv[q] = tX[cc * BT + tx + TX * q];
+        for (int q = 0; q < TB; ++q) xv[q] = tX[cc * BT + tx + TX * q];
 #pragma unroll
-      for (int i = 0; i < TR; ++i)
+        for (int i = 0; i < TR; ++i)
 #pragma unroll
-        for (int q = 0; q < TB; ++q) acc[i][q] = ADJ ? cmacc(acc[i][q], m[i], xv[q]) : cmac(acc[i][q], m[i], xv[q]);
+          for (int q = 0; q < TB; ++q) acc[i][q] = ADJ ? cmacc(acc[i][q], m[i], xv[q]) : cmac(acc[i][q], m[i], xv[q]);
+      }
     }
     __syncthreads();
+  }
+  if constexpr (G3) {
+#pragma unroll
+    for (int i = 0; i < TR; ++i)
+#pragma unroll
+      for (int q = 0; q < TB; ++q) acc[i][q] = Ops::fin(p1[i][q], p2[i][q], p3[i][q], ADJ);
   }
 #pragma unroll
   for (int i = 0; i < TR; ++i) {
@@ -409,22 +529,46 @@ __global__ void __launch_bounds__(256) k_stage_mm_pipe(StageArgs<V> a) {
 // thread tiles (<8,4,8> on 128 threads) a CTA covers 128 rows and 32 right-hand sides: 32
 // accumulators per thread, 128 FMAs per step of the column loop against 10 shared-memory loads
 // (6 in the adjoint), from the list of 128-row tiles, with chunks of 16 columns.
+//
+// Shared-memory layout of the 8 x 4 tiles (TX = 8: a warp holds 4 thread rows ty and 8 thread
+// columns tx).  Unpadded, the 4 ty of a warp read factor entries 64 bytes apart in the adjoint
+// (TR = 8 contiguous values each) or whole rows apart in the forward direction, and the 8 tx read
+// vector entries 32 bytes apart: two or four accesses per shared-memory bank.  Two complex
+// values of padding after every 8 factor columns (adjoint) or 8 factor rows (forward), and after
+// every 4 vector entries, put every access of a warp in a bank of its own (PA, PF, PX).  The
+// column indices of the next chunk's gathered rows are loaded into registers one chunk ahead, so
+// the cp.async copies of a chunk never wait for an index load.  The 8 x 4 tiles are held to 128
+// registers a thread, so that four CTAs (16 warps) share an SM.
 template <bool ADJ, int TX, int TB, int TR, int NT, int CK_ = 32>
 struct VtShape {
   static constexpr int TY = NT / TX, RT = TY * TR, BT = TX * TB, CK = CK_;
-  static constexpr int MROWS = ADJ ? CK : RT, MCOLS = ADJ ? RT : CK, MLD = MCOLS + 2;
-  static constexpr int SMEM = 2 * (MROWS * MLD + CK * BT) * 8;
+  static constexpr int MROWS = ADJ ? CK : RT, MCOLS = ADJ ? RT : CK;
+  static constexpr int PA = (ADJ && TR == 8 && TX == 8) ? 2 : 0;   // per 8 factor columns
+  static constexpr int PF = (!ADJ && TR == 8 && TX == 8) ? 2 : 0;  // per 8 factor rows
+  static constexpr int PX = (TB == 4 && TX == 8) ? 2 : 0;          // per 4 vector entries
+  static constexpr int MLD = MCOLS + 2 + (MCOLS / 8) * PA;
+  static constexpr int MTILE = MROWS * MLD + (MROWS / 8) * PF;
+  static constexpr int BTP = BT + (BT / 4) * PX;
+  static constexpr int XTILE = CK * BTP;
+  static constexpr int SMEM = 2 * (MTILE + XTILE) * 8;
+  // offset of factor entry (row mr, column mc) of a tile, and of vector entry j of chunk column cc
+  static __device__ __forceinline__ int mofs(int mr, int mc) {
+    return mr * MLD + (mr >> 3) * PF + mc + (mc >> 3) * PA;
+  }
+  static __device__ __forceinline__ int xofs(int cc, int j) { return cc * BTP + j + (j >> 2) * PX; }
 };
 
 template <bool ADJ, int TX, int TB, int TR, int NT, int CK_ = 32>
-__global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
+__global__ void __launch_bounds__(NT, NT == 128 && TX == 8 ? 4 : 1) k_stage_mm_vt(StageArgs<float2> a) {
   using S = VtShape<ADJ, TX, TB, TR, NT, CK_>;
   constexpr int RT = S::RT, BT = S::BT, CK = S::CK;
-  constexpr int MROWS = S::MROWS, MCOLS = S::MCOLS, MLD = S::MLD;
+  constexpr int MROWS = S::MROWS, MCOLS = S::MCOLS, MTILE = S::MTILE, XTILE = S::XTILE;
   static_assert(TB % 2 == 0 && TR % 2 == 0 && (RT == 64 || RT == 128), "tile shape");
+  static_assert(S::PA == 0 || TR == 8, "adjoint padding groups a thread's 8 rows");
+  static_assert(S::PX == 0 || TB == 4, "vector padding groups a thread's 4 right-hand sides");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* sM = reinterpret_cast<float2*>(smem_raw);
-  float2* sX = sM + 2 * MROWS * MLD;
+  float2* sX = sM + 2 * MTILE;
 
   int blk, tile, Rb, Cb;
   cta_work<float2, ADJ>(a, blk, tile, Rb, Cb);
@@ -439,8 +583,20 @@ __global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
   const int tx = tid % TX;
   const int ty = tid / TX;
 
+  // x pairs this thread copies per chunk, and the column indices of the next chunk's pairs
+  constexpr int CPX = BT / 2;
+  constexpr int NXP = (CK * CPX + NT - 1) / NT;
+  int nidx[NXP];
+  auto fetch_idx = [&](int c0) {
+#pragma unroll
+    for (int u = 0; u < NXP; ++u) {
+      const int e = tid + u * NT;
+      const int c = c0 + e / CPX;
+      nidx[u] = (e < CK * CPX && c < ncols) ? colidx[c] : -1;
+    }
+  };
   auto load = [&](int buf, int c0) {
-    float2* dM = sM + buf * MROWS * MLD;
+    float2* dM = sM + buf * MTILE;
     constexpr int CPR = MCOLS / 2;
     for (int e = tid; e < MROWS * CPR; e += NT) {
       const int mr = e / CPR;
@@ -448,21 +604,25 @@ __global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
       const int grow = (ADJ ? c0 : r0) + mr;
       const int gcol = (ADJ ? r0 : c0) + mc;
       const bool ok = grow < Rb && gcol < Cb;
-      cp_async16(dM + mr * MLD + mc, ok ? (const void*)(M + (size_t)grow * a.C + gcol) : (const void*)M,
+      cp_async16(dM + S::mofs(mr, mc), ok ? (const void*)(M + (size_t)grow * a.C + gcol) : (const void*)M,
                  ok ? 16 : 0);
     }
-    float2* dX = sX + buf * CK * BT;
-    constexpr int CPX = BT / 2;
-    for (int e = tid; e < CK * CPX; e += NT) {
-      const int cc = e / CPX;
-      const int jj = (e - cc * CPX) * 2;
-      const int c = c0 + cc, j = j0 + jj;
-      const int idx = c < ncols ? colidx[c] : -1;
-      const bool ok = idx >= 0 && j < a.b;
-      cp_async16(dX + cc * BT + jj, ok ? (const void*)(a.x + (long long)idx * a.xrs + j) : (const void*)a.x,
-                 ok ? 16 : 0);
+    float2* dX = sX + buf * XTILE;
+#pragma unroll
+    for (int u = 0; u < NXP; ++u) {
+      const int e = tid + u * NT;
+      if (e < CK * CPX) {
+        const int cc = e / CPX;
+        const int jj = (e - cc * CPX) * 2;
+        const int j = j0 + jj;
+        const int idx = nidx[u];
+        const bool ok = idx >= 0 && j < a.b;
+        cp_async16(dX + S::xofs(cc, jj), ok ? (const void*)(a.x + (long long)idx * a.xrs + j) : (const void*)a.x,
+                   ok ? 16 : 0);
+      }
     }
     cp_async_commit();
+    fetch_idx(c0 + CK);
   };
 
   float2 acc[TR][TB];
@@ -476,7 +636,10 @@ __global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
   const int cps = (nch + a.ksplit - 1) / a.ksplit;
   const int kb = min(nch, (int)blockIdx.z * cps);
   const int nchunks = min(nch, kb + cps) - kb;
-  if (nchunks > 0) load(0, kb * CK);
+  if (nchunks > 0) {
+    fetch_idx(kb * CK);
+    load(0, kb * CK);
+  }
   for (int k = 0; k < nchunks; ++k) {
     if (k + 1 < nchunks) {
       load((k + 1) & 1, (kb + k + 1) * CK);
@@ -485,25 +648,25 @@ __global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const float2* tM = sM + (k & 1) * MROWS * MLD;
-    const float2* tX = sX + (k & 1) * CK * BT;
+    const float2* tM = sM + (k & 1) * MTILE;
+    const float2* tX = sX + (k & 1) * XTILE;
 #pragma unroll 4
     for (int cc = 0; cc < CK; ++cc) {
       float2 m[TR], xv[TB];
       if (ADJ) {
 #pragma unroll
         for (int i = 0; i < TR; i += 2) {
-          const float4 v = *reinterpret_cast<const float4*>(tM + cc * MLD + ty * TR + i);
+          const float4 v = *reinterpret_cast<const float4*>(tM + S::mofs(cc, ty * TR + i));
           m[i] = make_float2(v.x, v.y);
           m[i + 1] = make_float2(v.z, v.w);
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < TR; ++i) m[i] = tM[(ty * TR + i) * MLD + cc];
+        for (int i = 0; i < TR; ++i) m[i] = tM[S::mofs(ty * TR + i, cc)];
       }
 #pragma unroll
       for (int q = 0; q < TB; q += 2) {
-        const float4 v = *reinterpret_cast<const float4*>(tX + cc * BT + tx * TB + q);
+        const float4 v = *reinterpret_cast<const float4*>(tX + S::xofs(cc, tx * TB + q));
         xv[q] = make_float2(v.x, v.y);
         xv[q + 1] = make_float2(v.z, v.w);
       }
@@ -528,6 +691,59 @@ __global__ void __launch_bounds__(NT) k_stage_mm_vt(StageArgs<float2> a) {
       const int j = j0 + tx * TB + q;
       if (j < a.b) dst[(long long)j * cs] = acc[i][q];
     }
+  }
+}
+
+// ---- small blocks (padded R, C <= 32, the 16-point leaf stages): one warp per block ------------
+// Lane j owns right-hand side j0 + j of the CTA's 32-wide tile.  The warp copies its block (R x C
+// values, coalesced) and the block's gathered input rows (ncols x 32 values, one coalesced row
+// per column) into shared memory, then every lane forms each output row as the plain sum over
+// the block's columns in order, with the multiply-adds of cmac / cmacc: the same operations in the
+// same order as the tiled kernels (which add only zeros beyond the valid columns), so the results
+// are bit-identical to theirs.  A 64- or 128-row tile would leave most of its rows idle on a
+// 16 x 16 block.  Dynamic shared memory: kSmallWarps x (R C + 32 cmax) values, cmax = C forward,
+// R adjoint.
+constexpr int kSmallWarps = 4;
+constexpr int kSmallMaxDim = 32;
+
+template <typename V, bool ADJ>
+__global__ void __launch_bounds__(32 * kSmallWarps) k_stage_small(StageArgs<V> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int blk = blockIdx.x * kSmallWarps + w;
+  if (blk >= a.nblk) return;  // warp-uniform; the kernel has no CTA-wide barrier
+  const int RC = a.R * a.C, cmax = ADJ ? a.R : a.C;
+  V* sm = reinterpret_cast<V*>(smem_raw) + (size_t)w * (RC + 32 * cmax);
+  V* sx = sm + RC;
+  int Rb = a.R, Cb = a.C;
+  if (a.dims) {
+    const int2 d = a.dims[blk];
+    Rb = d.x;
+    Cb = d.y;
+  }
+  const int nrows = ADJ ? Cb : Rb;
+  const int ncols = ADJ ? Rb : Cb;
+  const V* M = a.M + (size_t)blk * RC;
+  const int* rowidx = ADJ ? a.in + (size_t)blk * a.C : a.out + (size_t)blk * a.R;
+  const int* colidx = ADJ ? a.out + (size_t)blk * a.R : a.in + (size_t)blk * a.C;
+  for (int e = lane; e < RC; e += 32) sm[e] = M[e];
+  const int j = blockIdx.y * 32 + lane;
+  const bool on = j < a.b;
+#pragma unroll 4
+  for (int c = 0; c < ncols; ++c) {
+    const int idx = colidx[c];
+    sx[c * 32 + lane] = (idx >= 0 && on) ? a.x[(long long)idx * a.xrs + (long long)j * a.xcs] : czero<V>();
+  }
+  __syncwarp();
+  for (int r = 0; r < nrows; ++r) {
+    const int oidx = rowidx[r];
+    if (oidx < 0) continue;
+    V acc = czero<V>();
+    for (int c = 0; c < ncols; ++c) {
+      const V m = ADJ ? sm[c * a.C + r] : sm[r * a.C + c];
+      acc = ADJ ? cmacc(acc, m, sx[c * 32 + lane]) : cmac(acc, m, sx[c * 32 + lane]);
+    }
+    if (on) a.y[(long long)oidx * a.yrs + (long long)j * a.ycs] = acc;
   }
 }
 

@@ -27,11 +27,14 @@ from paper_2105_02995_gb300.builder.__main__ import build_cached  # noqa: E402
 from paper_2105_02995_gb300.inputs import complex_gaussian, rhs_seed  # noqa: E402
 
 CASES = {
-    # kind, n, eps_bf, eps_hif, dtype, K bound, direct-solve bound
-    "ex1_65536": ("ex1", 65536, 1e-7, 1e-6, torch.complex128, 2e-6, 2e-3),
-    "ex3_256": ("ex3", 256, 1e-4, 1e-3, torch.complex64, 2e-3, 1e-1),
-    # measured on the host with the oracle: sampled e_a 1.3e-10, direct-solve residual 3.9e-10
-    "ex1_16384_e9": ("ex1", 16384, 1e-10, 1e-9, torch.complex128, 5e-10, 2e-9),
+    # kind, n, eps_bf, eps_hif, dtype, K bound, direct-solve bound: about three times the values
+    # measured on a GB300 with these seeds (K-dot / K-dot* at sampled outputs; direct solve):
+    #   ex1_65536     2.1e-7 / 5.6e-8;   3.9e-7
+    #   ex3_256       3.0e-4 / 5.2e-4;   1.9e-3
+    #   ex1_16384_e9  1.3e-10 / 4.6e-11; 3.9e-10 (the same on the host with the oracle)
+    "ex1_65536": ("ex1", 65536, 1e-7, 1e-6, torch.complex128, 7e-7, 1.2e-6),
+    "ex3_256": ("ex3", 256, 1e-4, 1e-3, torch.complex64, 1.6e-3, 6e-3),
+    "ex1_16384_e9": ("ex1", 16384, 1e-10, 1e-9, torch.complex128, 4e-10, 1.2e-9),
 }
 TOL64, TOL32 = 1e-12, 2e-5  # as in tests/test_gpu_parity.py
 _ops = {}
@@ -121,7 +124,9 @@ def test_iterative_solve_full_size(name, method):
         assert it <= 30, infos
     fh = f.cpu().numpy()
     rows = np.sort(np.random.default_rng(6).choice(N, 48, replace=False))
-    assert rel(fo.K_rows(ofo, rows, fh), u[rows]) < 20 * kbound
+    res = rel(fo.K_rows(ofo, rows, fh), u[rows])
+    print(f"[{name}] iterative solve ({method}), sampled residual against K: {res:.3g}")
+    assert res < 20 * kbound
 
 
 def test_headline_config_vs_factor_oracle():

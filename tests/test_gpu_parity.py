@@ -328,10 +328,11 @@ def test_exact_initial_guess_needs_no_iteration(method):
 
 # Autotuner: every tile-shape variant sums each output's terms in the same order, so for b >= 5
 # the tuned applies must reproduce the built-in ones bit for bit (but for the split variant 12 of
-# the in-place stages); for b <= 4 the few-RHS kernel
-# (tree reductions) may be chosen, within the parity tolerances above.
-ALLOWED = {0: {0, 8, 1}, 1: {0, 1, 2}, 2: {0, 2, 3, 4}, 3: {0, 3, 5, 6, 9, 10, 11, 12},
-           4: {0, 3, 5, 6, 7, 9, 10, 11, 12}}
+# the in-place stages and the three-product variants 14-16); for b <= 4 the few-RHS kernel (tree
+# reductions) may be chosen, within the parity tolerances above.
+ALLOWED = {0: {0, 8, 1}, 1: {0, 1, 2, 13, 16}, 2: {0, 2, 3, 4, 13, 14, 16},
+           3: {0, 3, 5, 6} | set(range(9, 16)), 4: {0, 3, 5, 6, 7} | set(range(9, 16))}
+THREE_PRODUCTS = {14, 15, 16}
 
 
 def _bucket(b):
@@ -355,9 +356,9 @@ def test_autotune_choices_and_results(name, prec, dt, tol, b):
     for w, ref in (("K", fa.apply_Kdot), ("Kadj", fa.apply_Kdot_adj), ("inv", fa.apply_inv)):
         after = getattr(op, "apply_" + w)(xd, precision=prec)
         torch.cuda.synchronize()
-        # bit for bit unless the tuner split an in-place stage over its columns (variant 12:
-        # partial sums in another order; the in-place stages are in inv only)
-        if b >= 5 and (w != "inv" or 12 not in choices):
+        # bit for bit unless the tuner picked three products or split an in-place stage over its
+        # columns (12: partial sums in another order; the in-place stages are in inv only)
+        if b >= 5 and not THREE_PRODUCTS & set(choices) and (w != "inv" or 12 not in choices):
             assert torch.equal(after, before[w]), w
         assert rel(host(after), ref(P, x64)) < tol, w
 
@@ -378,15 +379,17 @@ def test_autotune_rejects_bad_arguments():
 @pytest.mark.parametrize("prec,dt", [(binding.FIO_P64, torch.complex128), (binding.FIO_P32, torch.complex64),
                                      (binding.FIO_PDF, torch.complex128)])
 def test_every_tile_shape_is_bit_identical(name, prec, dt):
-    """Each tile shape <TX,TB,TR> of the stage kernel sums every output's terms in the same
-    order, so pinning any of them reproduces the built-in choice bit for bit (b = 40: ragged RHS
-    tiles for every shape)."""
+    """Each tile shape <TX,TB,TR> of the stage kernel, and the warp-per-block kernel for small
+    blocks (13: the 16-point leaf stages), sums every output's terms in the same order, so pinning
+    any of them reproduces the built-in choice bit for bit (b = 40: ragged RHS tiles for every
+    shape)."""
     buf, info, P, op, ofo = get(name)
     b = 40
     xd = dev(complex_gaussian(ofo.N, b, rhs_seed(0, 700)), dt)
     op.set_variant(b, prec, 0)
     ref = {w: getattr(op, "apply_" + w)(xd, precision=prec).clone() for w in ("K", "Kadj", "inv")}
-    for var in list(range(1, 8)) + ([9, 10, 11] if prec == binding.FIO_P32 else []):
+    for var in list(range(1, 8)) + ([9, 10, 11] if prec == binding.FIO_P32 else []) + \
+            ([13] if prec != binding.FIO_PDF else []):
         op.set_variant(b, prec, var)
         for w in ("K", "Kadj", "inv"):
             y = getattr(op, "apply_" + w)(xd, precision=prec)
@@ -484,11 +487,57 @@ def test_fp32_split_inplace_stages(name, b):
         op.set_variant(b, binding.FIO_P32, 0)
 
 
+@pytest.mark.parametrize("name", ["ex1_256", "ex3_32", "ex3_64", "ex2b_1024"])
+@pytest.mark.parametrize("prec", [binding.FIO_P64, binding.FIO_PDF])
+@pytest.mark.parametrize("b", [6, 17, 40])
+def test_three_product_fp64_and_double_float(name, prec, b):
+    """Variants 14-16 (three real products per complex product in FP64 and double-float, on the
+    butterfly stages): every apply within the bound of its arithmetic against the oracle (FP64
+    1e-12; double-float as the four-product test: max(1e-12, 4 sqrt(longest sum) 2^5 e64)), K-dot
+    and K-dot* within three times the four-product error plus 1e-15, and G-dot bit-identical to
+    the built-in choice (the in-place stages keep four products)."""
+    buf, info, P, op, ofo = get(name)
+    x = complex_gaussian(ofo.N, b, rhs_seed(0, 910 + b))
+    xd = dev(x)
+    refs = (("K", fa.apply_Kdot), ("Kadj", fa.apply_Kdot_adj), ("G", fa.apply_G), ("inv", fa.apply_inv))
+    want = {w: oref(P, x) for w, oref in refs}
+    ratio = 4 * np.sqrt(longest_sum(P)) * 2.0 ** 5
+    try:
+        op.set_variant(b, prec, 0)
+        four = {w: getattr(op, "apply_" + w)(xd, precision=prec).clone() for w, _ in refs}
+        e64 = {w: rel(host(getattr(op, "apply_" + w)(xd)), want[w]) for w, _ in refs}
+        for var in (14, 15, 16):
+            op.set_variant(b, prec, var)
+            for w, _ in refs:
+                y = getattr(op, "apply_" + w)(xd, precision=prec)
+                torch.cuda.synchronize()
+                err, e4 = rel(host(y), want[w]), rel(host(four[w]), want[w])
+                print(f"[{name} {prec} b={b} variant {var}] {w}: {err:.3g} (four products {e4:.3g})")
+                bound = TOL64 if prec == binding.FIO_P64 else max(TOL64, ratio * e64[w])
+                assert err < bound, (var, w, err, e64[w])
+                if w == "G":
+                    assert torch.equal(y, four[w]), var
+                elif w in ("K", "Kadj"):
+                    assert err <= 3 * e4 + 1e-15, (var, w, err, e4)
+    finally:
+        op.set_variant(b, prec, 0)
+
+
 def test_set_variant_rejects_unknown_variants():
     buf, info, P, op, ofo = get("ex3_32")
     lib = binding.load()
-    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 13) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 17) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 14) == -1   # FP64 / double-float tiles
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_PDF, 16) == 0
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_PDF, 0) == 0
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 14) == 0
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 13) == 0
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 13) == 0
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_PDF, 13) == -1   # double-float: tiled kernels only
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 12) == -1   # complex64-only tiles
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 0) == 0
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 12) == 0
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 0) == 0
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 11) == -1   # complex64-only tiles
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 9) == -1    # complex64-only tiles
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 8) == -1    # few-RHS kernel needs b <= 4
