@@ -1243,12 +1243,17 @@ extern "C" int fio_apply_inv_host(fio_op op, const void* u_host, void* f_host, i
   if (rc) return rc;
   void *U = bufs[3], *F = bufs[4];
   const size_t w = (size_t)op->N * es;
-  if (cudaMemcpy2DAsync(U, w, u_host, (size_t)ld * es, w, (size_t)b, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return FIO_ECUDA;
+  // one contiguous copy each way when the caller's columns are packed (ld == N)
+  const cudaError_t e_in = ld == op->N
+      ? cudaMemcpyAsync(U, u_host, w * (size_t)b, cudaMemcpyHostToDevice, s)
+      : cudaMemcpy2DAsync(U, w, u_host, (size_t)ld * es, w, (size_t)b, cudaMemcpyHostToDevice, s);
+  if (e_in != cudaSuccess) return FIO_ECUDA;
   rc = fio_apply_internal(op, W_INV, U, F, op->N, b, precision, s);
   if (rc) return rc;
-  if (cudaMemcpy2DAsync(f_host, (size_t)ld * es, F, w, w, (size_t)b, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return FIO_ECUDA;
+  const cudaError_t e_out = ld == op->N
+      ? cudaMemcpyAsync(f_host, F, w * (size_t)b, cudaMemcpyDeviceToHost, s)
+      : cudaMemcpy2DAsync(f_host, (size_t)ld * es, F, w, w, (size_t)b, cudaMemcpyDeviceToHost, s);
+  if (e_out != cudaSuccess) return FIO_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return FIO_ECUDA;
   // a tensor-core bounded wait that gave up left part of f unwritten: report it here, at the
   // call that produced the result, not at some later synchronising call
