@@ -644,9 +644,10 @@ bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
 // k_stage_small (a warp per block, FP64 and FP32, padded blocks up to 32 x 32); 14, 15, 16 the
 // FP64 and double-float tiles of 3, 6, 2 with three real products per complex product
 // (k_stage_mm_pipe's G3) on the butterfly stages (the in-place stages, where the HIF's
-// conditioning amplifies rounding, keep four products).  Shapes 2..7, 9..12, 14..16 need the
-// pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the plain
-// tiled kernel.
+// conditioning amplifies rounding, keep four products); 17 the tile of 9 with 16-column chunks
+// (half the shared memory: up to five CTAs per SM instead of two).  Shapes 2..7, 9..12, 14..17
+// need the pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the
+// plain tiled kernel.
 // the TMA-fed persistent tensor-core kernel (k_stage_tma): 30 units of as many row tiles as tensor
 // memory holds and the deepest A ring; 31 the same with in-place stages split over K; 32 units
 // sized for about eight per SM; 33 an A ring of at most six slots (split TF32: a six-slot tail
@@ -662,14 +663,16 @@ constexpr int kFp32CoresVariant = 40;
 inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : (b <= 32 ? 3 : 4))); }
 // candidates per bucket, the built-in choice first
 constexpr int kSmallVariant = 13;
-constexpr int kMaxCudaCoreVariant = 16;
+constexpr int kVtChunk16Variant = 17;
+constexpr int kMaxCudaCoreVariant = 17;
+inline bool is_fp32_tile_variant(int v) { return (v >= 9 && v <= 12) || v == kVtChunk16Variant; }
 inline bool is_3m_variant(int v) { return v >= 14 && v <= 16; }
 // the four-product variant a three-product one stands for on the in-place stages
 inline int four_product_of(int v) { return v == 14 ? 3 : v == 15 ? 6 : v == 16 ? 2 : v; }
-constexpr int kNCand = 11;
+constexpr int kNCand = 12;
 constexpr int kCand[5][kNCand] = {{8, 1}, {1, 2, 13, 16}, {2, 4, 3, 13, 14, 16},
-                                  {3, 5, 6, 9, 10, 11, 12, 13, 14, 15},
-                                  {3, 5, 6, 7, 9, 10, 11, 12, 13, 14, 15}};
+                                  {3, 5, 6, 9, 10, 11, 12, 13, 14, 15, 17},
+                                  {3, 5, 6, 7, 9, 10, 11, 12, 13, 14, 15, 17}};
 
 // launch with variant `var`; false when it does not apply to this launch
 template <typename V, bool ADJ>
@@ -695,6 +698,7 @@ bool launch_variant(const StageArgs<V>& a, cudaStream_t s, int var) {
     case 14: return pipe && launch_pipe3<V, ADJ, 16, 2, 4>(a, s);
     case 15: return pipe && launch_pipe3<V, ADJ, 32, 1, 8>(a, s);
     case 16: return pipe && launch_pipe3<V, ADJ, 16, 1, 4>(a, s);
+    case kVtChunk16Variant: return pipe && launch_vt_if<V, ADJ, 16, 2, 8, 128, 16>(a, s);
     default: return false;
   }
 }
@@ -706,7 +710,7 @@ bool variant_applies(const StageArgs<V>& a, int var) {
   if (var == 1) return true;
   if (var >= 2 && var <= 7) return pipe;
   if (var == 8) return a.b <= kVecMaxRhs;
-  if (var >= 9 && var <= 12) return pipe && std::is_same<V, float2>::value && (var < 11 || a.tiles128);
+  if (is_fp32_tile_variant(var)) return pipe && std::is_same<V, float2>::value && ((var != 11 && var != 12) || a.tiles128);
   if (var == kSmallVariant) return small_ok(a);
   if (is_3m_variant(var)) return pipe && !std::is_same<V, float2>::value;
   return false;
@@ -1325,6 +1329,14 @@ extern "C" int fio_apply_profiled(fio_op op, int which, const void* x, void* y, 
 // ---------------------------------------------------------------------------------------------
 namespace {
 
+// L2 flush of the autotuner: a write larger than the 129 MB L2 before every timed launch, so that
+// a stage is timed with its factor coming from HBM, as in an apply (where the stages before it
+// have streamed the rest of the factors through L2); small stages would otherwise be timed on
+// L2-resident data and the choice between close variants would follow a regime the apply never
+// sees
+constexpr size_t kTuneFlushBytes = 256ull << 20;
+thread_local void* g_tune_flush = nullptr;  // set by fio_autotune for the duration of the call
+
 // time a launcher (best of 3 after one warm-up): the launcher returns false when its variant does
 // not apply (-1); -2 on a CUDA error
 template <typename F>
@@ -1332,6 +1344,7 @@ float time_launch(F&& launch, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   if (!launch()) return -1.f;
   float best = -1.f;
   for (int rep = 0; rep < 3; ++rep) {
+    if (g_tune_flush) cudaMemsetAsync(g_tune_flush, rep, kTuneFlushBytes, s);
     cudaEventRecord(e0, s);
     launch();
     cudaEventRecord(e1, s);
@@ -1447,7 +1460,7 @@ extern "C" int fio_set_variant(fio_op op, int b, int precision, int variant) {
   } else {
     ti = precision == FIO_P64 ? 0 : (precision == FIO_PDF ? 2 : 1);
     if (variant < 0 || variant > kMaxCudaCoreVariant || (variant == 8 && b > kVecMaxRhs) ||
-        (variant >= 9 && variant < kSmallVariant && ti != 1) || (variant == kSmallVariant && ti == 2) ||
+        (is_fp32_tile_variant(variant) && ti != 1) || (variant == kSmallVariant && ti == 2) ||
         (is_3m_variant(variant) && ti == 1))
       return FIO_EINVAL;
   }
@@ -1466,6 +1479,13 @@ extern "C" int fio_autotune(fio_op op, int b, int precision, void* stream, int* 
   if (b == 0) return FIO_OK;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaGetLastError() != cudaSuccess) return FIO_ECUDA;
+  // the L2 flush target (without device memory for it, the launches are timed unflushed)
+  void* flush = nullptr;
+  if (cudaMalloc(&flush, kTuneFlushBytes) != cudaSuccess) {
+    cudaGetLastError();
+    flush = nullptr;
+  }
+  g_tune_flush = flush;
   int rc;
   if (precision == FIO_P64) {
     rc = tune_type<double2>(op, b, s, choices, cap, nchoices);
@@ -1475,7 +1495,9 @@ extern "C" int fio_autotune(fio_op op, int b, int precision, void* stream, int* 
     TcMode m(tc_mode_of(precision));
     rc = tune_type<float2>(op, b, s, choices, cap, nchoices);
   }
-  if (rc == FIO_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = FIO_ECUDA;
+  g_tune_flush = nullptr;
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == FIO_OK) rc = FIO_ECUDA;
+  if (flush) cudaFree(flush);
   return rc;
 }
 
