@@ -203,7 +203,8 @@ int fio_solve(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
  * 16 (FP64 and double-float) the tiles of 3 / 6 / 2 with three real products per complex
  * product on the butterfly stages (Gauss's 3M form: the imaginary part's rounding error up to a
  * few times the four-product one; the in-place HIF stages keep four products), 17 (FP32) the
- * tiles of 9 with 16-column chunks; with a tensor-core
+ * tiles of 9 with 16-column chunks, 18 (FP32) the tiles of 11 without their register cap (three
+ * CTAs per SM instead of four); with a tensor-core
  * precision and b >= 8: 0 the single-buffer tcgen05 kernel, 20 / 21 / 22 its warp-specialised
  * ring variant with 2 / 3 / 4 chunk stages, 30 the persistent tcgen05 kernel whose factor tiles
  * arrive by TMA (work units of as many 128-row tiles as tensor memory holds, deepest ring), 31
@@ -222,8 +223,8 @@ int fio_solve(fio_op op, const void* u, void* f, int64_t ld, int b, int dtype,
 int fio_autotune(fio_op op, int b, int precision, void* stream, int* choices, int cap, int* nchoices);
 
 /* Pin the kernel variant of every stage launch of (precision, the bucket of b) to `variant`
- * (0 = the built-in choice): 1..17 as for fio_autotune on the CUDA cores (8 only for b <= 4,
- * 9..12 and 17 only for FIO_P32, 13 not for FIO_PDF, 14..16 only for FIO_P64 and FIO_PDF); with a tensor-core precision and b >= 8, 0 (single-buffer kernel),
+ * (0 = the built-in choice): 1..18 as for fio_autotune on the CUDA cores (8 only for b <= 4,
+ * 9..12, 17, 18 only for FIO_P32, 13 not for FIO_PDF, 14..16 only for FIO_P64 and FIO_PDF); with a tensor-core precision and b >= 8, 0 (single-buffer kernel),
  * 20, 21, 22 (the warp-specialised ring kernel with 2, 3, 4 chunk stages), 30..33 (the
  * TMA-fed persistent kernel, as for fio_autotune) or 40 (FP32 CUDA cores); a variant that does not apply to a stage
  * (shared memory, alignment, odd b) falls back to 0.  Host-only; FIO_EINVAL for a variant that

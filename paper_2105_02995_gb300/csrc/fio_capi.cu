@@ -552,7 +552,7 @@ bool launch_pipe3(StageArgs<V> a, cudaStream_t s) {
 
 // complex64 tiles with contiguous per-thread rows and right-hand sides (k_stage_mm_vt); 64- or
 // 128-row tiles (the latter from the stage's list of 128-row tiles)
-template <bool ADJ, int TX, int TB, int TR, int NT, int CK = 32>
+template <bool ADJ, int TX, int TB, int TR, int NT, int CK = 32, int MINB = (NT == 128 && TX == 8 ? 4 : 1)>
 bool launch_vt(StageArgs<float2> a, cudaStream_t s) {
   using S = VtShape<ADJ, TX, TB, TR, NT, CK>;
   static_assert(S::RT == kTileRows || S::RT == 2 * kTileRows, "tile lists hold 64- and 128-row tiles");
@@ -561,19 +561,20 @@ bool launch_vt(StageArgs<float2> a, cudaStream_t s) {
     a.tiles = a.tiles128;
     a.ntiles_list = a.ntiles128;
   }
-  if (!smem_opt_in((const void*)k_stage_mm_vt<ADJ, TX, TB, TR, NT, CK>, S::SMEM)) return false;
+  if (!smem_opt_in((const void*)k_stage_mm_vt<ADJ, TX, TB, TR, NT, CK, MINB>, S::SMEM)) return false;
   const int nrows = ADJ ? a.C : a.R;
   a.ntiles = (nrows + S::RT - 1) / S::RT;
   const long long ncta = a.tiles ? a.ntiles_list : (long long)a.nblk * a.ntiles;
   if (ncta == 0) return true;
   dim3 grid((unsigned)ncta, (unsigned)((a.b + S::BT - 1) / S::BT), (unsigned)a.ksplit);
-  k_stage_mm_vt<ADJ, TX, TB, TR, NT, CK><<<grid, NT, S::SMEM, s>>>(a);
+  k_stage_mm_vt<ADJ, TX, TB, TR, NT, CK, MINB><<<grid, NT, S::SMEM, s>>>(a);
   return true;
 }
-template <typename V, bool ADJ, int TX, int TB, int TR, int NT, int CK = 32>
+template <typename V, bool ADJ, int TX, int TB, int TR, int NT, int CK = 32,
+          int MINB = (NT == 128 && TX == 8 ? 4 : 1)>
 bool launch_vt_if(const StageArgs<V>& a, cudaStream_t s) {
   if constexpr (std::is_same<V, float2>::value) {
-    return launch_vt<ADJ, TX, TB, TR, NT, CK>(a, s);
+    return launch_vt<ADJ, TX, TB, TR, NT, CK, MINB>(a, s);
   } else {
     return false;
   }
@@ -645,7 +646,8 @@ bool launch_vec(const StageArgs<V>& a, cudaStream_t s) {
 // FP64 and double-float tiles of 3, 6, 2 with three real products per complex product
 // (k_stage_mm_pipe's G3) on the butterfly stages (the in-place stages, where the HIF's
 // conditioning amplifies rounding, keep four products); 17 the tile of 9 with 16-column chunks
-// (half the shared memory: up to five CTAs per SM instead of two).  Shapes 2..7, 9..12, 14..17
+// (half the shared memory: up to five CTAs per SM instead of two); 18 the tile of 11 without its
+// register cap (three CTAs per SM).  Shapes 2..7, 9..12, 14..17
 // need the pipelined kernel's layout (row-major, 16-byte aligned rows); shape 1 falls back to the
 // plain tiled kernel.
 // the TMA-fed persistent tensor-core kernel (k_stage_tma): 30 units of as many row tiles as tensor
@@ -664,15 +666,16 @@ inline int rhs_bucket(int b) { return b <= 4 ? 0 : (b <= 8 ? 1 : (b <= 16 ? 2 : 
 // candidates per bucket, the built-in choice first
 constexpr int kSmallVariant = 13;
 constexpr int kVtChunk16Variant = 17;
-constexpr int kMaxCudaCoreVariant = 17;
-inline bool is_fp32_tile_variant(int v) { return (v >= 9 && v <= 12) || v == kVtChunk16Variant; }
+constexpr int kVtUncappedVariant = 18;
+constexpr int kMaxCudaCoreVariant = 18;
+inline bool is_fp32_tile_variant(int v) { return (v >= 9 && v <= 12) || v == kVtChunk16Variant || v == kVtUncappedVariant; }
 inline bool is_3m_variant(int v) { return v >= 14 && v <= 16; }
 // the four-product variant a three-product one stands for on the in-place stages
 inline int four_product_of(int v) { return v == 14 ? 3 : v == 15 ? 6 : v == 16 ? 2 : v; }
-constexpr int kNCand = 12;
+constexpr int kNCand = 13;
 constexpr int kCand[5][kNCand] = {{8, 1}, {1, 2, 13, 16}, {2, 4, 3, 13, 14, 16},
-                                  {3, 5, 6, 9, 10, 11, 12, 13, 14, 15, 17},
-                                  {3, 5, 6, 7, 9, 10, 11, 12, 13, 14, 15, 17}};
+                                  {3, 5, 6, 9, 10, 11, 12, 13, 14, 15, 17, 18},
+                                  {3, 5, 6, 7, 9, 10, 11, 12, 13, 14, 15, 17, 18}};
 
 // launch with variant `var`; false when it does not apply to this launch
 template <typename V, bool ADJ>
@@ -699,6 +702,7 @@ bool launch_variant(const StageArgs<V>& a, cudaStream_t s, int var) {
     case 15: return pipe && launch_pipe3<V, ADJ, 32, 1, 8>(a, s);
     case 16: return pipe && launch_pipe3<V, ADJ, 16, 1, 4>(a, s);
     case kVtChunk16Variant: return pipe && launch_vt_if<V, ADJ, 16, 2, 8, 128, 16>(a, s);
+    case kVtUncappedVariant: return pipe && launch_vt_if<V, ADJ, 8, 4, 8, 128, 16, 1>(a, s);
     default: return false;
   }
 }
@@ -710,7 +714,8 @@ bool variant_applies(const StageArgs<V>& a, int var) {
   if (var == 1) return true;
   if (var >= 2 && var <= 7) return pipe;
   if (var == 8) return a.b <= kVecMaxRhs;
-  if (is_fp32_tile_variant(var)) return pipe && std::is_same<V, float2>::value && ((var != 11 && var != 12) || a.tiles128);
+  if (is_fp32_tile_variant(var))
+    return pipe && std::is_same<V, float2>::value && ((var != 11 && var != 12 && var != kVtUncappedVariant) || a.tiles128);
   if (var == kSmallVariant) return small_ok(a);
   if (is_3m_variant(var)) return pipe && !std::is_same<V, float2>::value;
   return false;

@@ -538,7 +538,8 @@ __global__ void __launch_bounds__(256) k_stage_mm_pipe(StageArgs<V> a) {
 // every 4 vector entries, put every access of a warp in a bank of its own (PA, PF, PX).  The
 // column indices of the next chunk's gathered rows are loaded into registers one chunk ahead, so
 // the cp.async copies of a chunk never wait for an index load.  The 8 x 4 tiles are held to 128
-// registers a thread, so that four CTAs (16 warps) share an SM.
+// registers a thread by default (MINB = 4 CTAs, 16 warps, per SM); MINB = 1 lets the compiler
+// use more (the adjoint then takes about 155, three CTAs per SM).
 template <bool ADJ, int TX, int TB, int TR, int NT, int CK_ = 32>
 struct VtShape {
   static constexpr int TY = NT / TX, RT = TY * TR, BT = TX * TB, CK = CK_;
@@ -558,8 +559,8 @@ struct VtShape {
   static __device__ __forceinline__ int xofs(int cc, int j) { return cc * BTP + j + (j >> 2) * PX; }
 };
 
-template <bool ADJ, int TX, int TB, int TR, int NT, int CK_ = 32>
-__global__ void __launch_bounds__(NT, NT == 128 && TX == 8 ? 4 : 1) k_stage_mm_vt(StageArgs<float2> a) {
+template <bool ADJ, int TX, int TB, int TR, int NT, int CK_ = 32, int MINB = (NT == 128 && TX == 8 ? 4 : 1)>
+__global__ void __launch_bounds__(NT, MINB) k_stage_mm_vt(StageArgs<float2> a) {
   using S = VtShape<ADJ, TX, TB, TR, NT, CK_>;
   constexpr int RT = S::RT, BT = S::BT, CK = S::CK;
   constexpr int MROWS = S::MROWS, MCOLS = S::MCOLS, MTILE = S::MTILE, XTILE = S::XTILE;

@@ -331,7 +331,7 @@ def test_exact_initial_guess_needs_no_iteration(method):
 # the in-place stages and the three-product variants 14-16); for b <= 4 the few-RHS kernel (tree
 # reductions) may be chosen, within the parity tolerances above.
 ALLOWED = {0: {0, 8, 1}, 1: {0, 1, 2, 13, 16}, 2: {0, 2, 3, 4, 13, 14, 16},
-           3: {0, 3, 5, 6, 17} | set(range(9, 16)), 4: {0, 3, 5, 6, 7, 17} | set(range(9, 16))}
+           3: {0, 3, 5, 6, 17, 18} | set(range(9, 16)), 4: {0, 3, 5, 6, 7, 17, 18} | set(range(9, 16))}
 THREE_PRODUCTS = {14, 15, 16}
 
 
@@ -388,7 +388,7 @@ def test_every_tile_shape_is_bit_identical(name, prec, dt):
     xd = dev(complex_gaussian(ofo.N, b, rhs_seed(0, 700)), dt)
     op.set_variant(b, prec, 0)
     ref = {w: getattr(op, "apply_" + w)(xd, precision=prec).clone() for w in ("K", "Kadj", "inv")}
-    for var in list(range(1, 8)) + ([9, 10, 11, 17] if prec == binding.FIO_P32 else []) + \
+    for var in list(range(1, 8)) + ([9, 10, 11, 17, 18] if prec == binding.FIO_P32 else []) + \
             ([13] if prec != binding.FIO_PDF else []):
         op.set_variant(b, prec, var)
         for w in ("K", "Kadj", "inv"):
@@ -526,8 +526,10 @@ def test_three_product_fp64_and_double_float(name, prec, b):
 def test_set_variant_rejects_unknown_variants():
     buf, info, P, op, ofo = get("ex3_32")
     lib = binding.load()
-    assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 18) == -1
-    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 18) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 19) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 19) == -1
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 18) == -1   # complex64-only tiles
+    assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 18) == 0
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P64, 17) == -1   # complex64-only tiles
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 17) == 0
     assert lib.fio_set_variant(op.h, 16, binding.FIO_P32, 0) == 0

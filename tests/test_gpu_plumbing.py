@@ -98,7 +98,7 @@ def test_host_buffer_entry_is_exact(b):
 @pytest.mark.parametrize("prec,dtype,variants", [
     (binding.FIO_P64, torch.complex128, list(range(1, 8)) + [13, 14, 15, 16]),
     (binding.FIO_PDF, torch.complex128, list(range(1, 8)) + [14, 15, 16]),
-    (binding.FIO_P32, torch.complex64, list(range(1, 8)) + list(range(9, 14)) + [17]),
+    (binding.FIO_P32, torch.complex64, list(range(1, 8)) + list(range(9, 14)) + [17, 18]),
     (binding.FIO_PTF32, torch.complex64, [20, 21, 22, 30, 31, 32, 33]),
     (binding.FIO_PBF16, torch.complex64, [20, 21, 22, 30, 31, 32, 33]),
     (binding.FIO_PTF32X3, torch.complex64, [20, 21, 22, 30, 31, 32, 33])])
@@ -152,7 +152,7 @@ def test_large_exact_operator_every_variant(prec, b):
     x = int_inputs(P.N, b, 6000 + b)
     xd = binding.colmajor(torch.from_numpy(x).to("cuda", torch.complex64))
     want = {"K": fa.apply_Kdot(P, x), "Kadj": fa.apply_Kdot_adj(P, x)}
-    variants = list(range(1, 8)) + list(range(9, 14)) + [17] if prec == binding.FIO_P32 else [0, 20, 30, 31, 32, 33, 40]
+    variants = list(range(1, 8)) + list(range(9, 14)) + [17, 18] if prec == binding.FIO_P32 else [0, 20, 30, 31, 32, 33, 40]
     try:
         for var in variants:
             op.set_variant(b, prec, var)
