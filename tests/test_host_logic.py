@@ -1,5 +1,5 @@
-"""Host-side logic that needs no GPU: the bench's workload naming and traffic guard, the serving
-loop's request generator, and the seeded input generator."""
+"""Host-side logic that needs no GPU: the bench's workload naming, traffic guard and solve
+summary, the serving loop's request generator, and the seeded input generator."""
 
 import argparse
 import hashlib
@@ -43,6 +43,28 @@ def test_bench_traffic_guard_follows_the_kernel_source():
         assert isinstance(bench.measured_traffic(), int) and bench.measured_traffic() > 0
     else:
         assert bench.measured_traffic() is None
+
+
+def _solve(rhs, ok=True, rr=3e-11, rr64=3e-11):
+    return {"statuses_ok": ok, "relres_max": rr, "relres_fp64_check": rr64, "rhs_per_s": rhs,
+            "p50_ms": 1.0, "p99_ms": 1.1}
+
+
+def test_bench_solve_summary_compares_at_equal_residual():
+    """The summary's best mixed path is the fastest of those that converged to 1e-10 on every
+    right-hand side (reported status and the FP64 recheck), and the plain path must converge."""
+    solves = {"plain_fp64_pcg_b1": _solve(17.0),
+              "ir_bf16_inner_dfres_b32": _solve(900.0, ok=False),              # stopped early
+              "ir_tf32_inner_dfres_b32": _solve(800.0, rr64=3e-9),             # FP64 recheck fails
+              "ir_split_tf32_inner_dfres_b128": _solve(240.0),
+              "gmres_fp32_precond_b32": _solve(25.0),
+              "error": "ignored"}
+    sm = bench.solve_summary(solves)
+    assert sm["best"] == "ir_split_tf32_inner_dfres_b128" and sm["rhs_per_s_ratio"] == round(240.0 / 17.0, 2)
+    assert "error" in bench.solve_summary({**solves, "plain_fp64_pcg_b1": _solve(17.0, rr=2e-10)})
+    assert "error" in bench.solve_summary({"plain_fp64_pcg_b1": _solve(17.0),
+                                           "ir_bf16_inner_dfres_b32": _solve(900.0, ok=False)})
+    assert bench.solve_converged(_solve(1.0, rr64=1.04e-10)) and not bench.solve_converged(_solve(1.0, rr64=1.06e-10))
 
 
 class _Op:
